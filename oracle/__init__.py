@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for the HDCG hot path (arXiv 1402.2585).
+
+TEST INFRASTRUCTURE.  This package is the plain, slow, obviously correct
+definition that the CUDA library is checked against.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py`` (its ``cpu_baseline`` leg and
+``--impl reference``) may import it.  The library never does, and it shares
+no code with the CUDA path: both sides only share the seeded input
+generators in ``synthetic/``.
+
+Modules
+-------
+``dwf``      lattice indexing, gamma matrices, Wilson hop, Moebius/Shamir
+             s-direction operators, the Schur-complement operator Mpc, its
+             adjoint and H = Mpc^dag Mpc (Sec. 4, Eq. for the Hermitian
+             red-black operator).
+``coarse``   blocks, block Gram-Schmidt, restriction / prolongation, the
+             little Dirac operator by brute force and by the Fourier trick,
+             the coarse stencil apply (Sec. 2, Sec. 5.1, Sec. 5.1.1).
+``solvers``  CG, the infra-red shifted smoother M_IRS, inverse-iteration
+             subspace, A-DEF2 with flexible beta (Figs. pcg / pcg_general,
+             Table algos, Sec. 4.3).
+
+Parity status of each function is stated in its docstring; every function
+here is pinned by a ``-m "not gpu"`` test except where marked
+"parity unpinned".
+"""

@@ -1,0 +1,210 @@
+"""FP64 oracle: Krylov solvers of the HDCG method.
+
+TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
+
+* ``cg``       textbook (Hestenes-Stiefel) conjugate gradients on an HPD operator.
+* ``mirs``     the infra-red shifted smoother M_IRS(H, N, lambda) = (H + lambda)^-1
+               truncated to N CG iterations from a zero start (Sec. 4.3).
+* ``inverse_iteration_subspace``  Gaussian vectors refined by steps of
+               (H + lambda_s)^-1 and block Gram-Schmidt after each step
+               (Sec. 1 and Sec. 5.2.1 name inverse iteration; step count,
+               shift and tolerance are readings, not values printed by the paper).
+* ``DeflationSpace``  Q = P A^-1 R (Sec. 2) with the coarse solve by CG to a
+               relative residual (Table optimised: 0.04 inside the solver) or exact.
+* ``adef2``    generalised preconditioned CG of Fig. pcg_general with the
+               A-DEF2 row of Table algos: V_start = Q b + P_R x, M_1 = P_R M_IRS + Q,
+               M_2 = M_3 = 1.  ``flexible=True`` uses the Polak-Ribiere
+               (flexible CG) beta = (r_{k+1}, y_{k+1} - y_k) / (r_k, y_k); the
+               paper cites Notay's flexible CG without printing beta (reading).
+
+Random numbers drawn by the method (the Gaussian start vectors of the
+subspace) are inputs to these functions.
+
+Parity: cg, mirs, DeflationSpace and adef2 are pinned by
+tests/test_oracle_solvers.py (true residual, free-field exact solution,
+A-DEF2 invariants Q r_k = 0 and P_L r_k = r_k with exact Q, QH = 1 - P_R in
+the block form of Sec. 2, deflated and undeflated solutions equal).
+The iteration counts themselves are parity unpinned (the paper's counts use
+gauge configurations that are not available).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .coarse import Blocking, block_gram_schmidt, coarse_apply, prolong, restrict, stencil_to_dense
+
+
+def _dot(a, b):
+    return complex(np.vdot(a.ravel(), b.ravel()))
+
+
+def _n2(a):
+    return float(np.vdot(a.ravel(), a.ravel()).real)
+
+
+def cg(apply_A, b, tol, maxiter=100000, x0=None, history=None):
+    """Solve A x = b (A HPD) until ||b - A x|| <= tol ||b|| (recursive residual).
+
+    Returns (x, iterations).  The caller recomputes the true residual.
+    """
+    x = np.zeros_like(b) if x0 is None else np.array(x0, copy=True)
+    r = b - apply_A(x) if x0 is not None else np.array(b, copy=True)
+    p = r.copy()
+    rr = _n2(r)
+    bb = _n2(b)
+    if bb == 0.0:
+        return x, 0
+    stop = tol * tol * bb
+    it = 0
+    while rr > stop and it < maxiter:
+        w = apply_A(p)
+        alpha = rr / _dot(p, w).real
+        x = x + alpha * p
+        r = r - alpha * w
+        rr_new = _n2(r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+        if history is not None:
+            history.append(np.sqrt(rr / bb))
+    return x, it
+
+
+def mirs(apply_H, r, n_iter: int = 7, shift: float = 1.0):
+    """M_IRS(H, N, lambda) r: exactly ``n_iter`` CG iterations on (H + lambda) from zero."""
+    x = np.zeros_like(r)
+    res = np.array(r, copy=True)
+    p = res.copy()
+    rr = _n2(res)
+    for _ in range(n_iter):
+        if rr == 0.0:
+            break
+        w = apply_H(p) + shift * p
+        alpha = rr / _dot(p, w).real
+        x = x + alpha * p
+        res = res - alpha * w
+        rr_new = _n2(res)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
+def inverse_iteration_subspace(apply_H, noise, blocking: Blocking, steps: int = 3,
+                               shift: float = 0.0, tol: float = 1e-4, maxiter: int = 100000):
+    """Subspace by inverse iteration: phi <- block_GS((H + shift)^-1 phi), ``steps`` times.
+
+    ``noise`` (Nvec, V/2, Ls, 4, 3) are the Gaussian start vectors.
+    """
+    phi = np.array(noise, dtype=np.complex128, copy=True)
+    Hs = (lambda v: apply_H(v) + shift * v) if shift else apply_H
+    for _ in range(steps):
+        for k in range(phi.shape[0]):
+            phi[k], _ = cg(Hs, phi[k], tol, maxiter)
+        phi = block_gram_schmidt(phi, blocking)
+    return phi
+
+
+@dataclass
+class DeflationSpace:
+    """Q = sum_{ab} |phi^a> (A^-1)^{ab} <phi^b| (Sec. 2) on an orthonormal block basis."""
+
+    phi: np.ndarray
+    blocking: Blocking
+    A: np.ndarray                  # canonical stencil [Vc][81][N][N]
+    coarse_tol: float = 0.0        # 0 -> exact dense solve
+    coarse_maxiter: int = 100000
+    coarse_iters: list = field(default_factory=list)
+
+    def __post_init__(self):
+        self._dense = None
+
+    def dense(self):
+        if self._dense is None:
+            D = stencil_to_dense(self.A, self.blocking)
+            n = D.shape[0] * D.shape[1]
+            self._dense = D.reshape(n, n)
+        return self._dense
+
+    def coarse_solve(self, c):
+        if self.coarse_tol == 0.0:
+            return np.linalg.solve(self.dense(), c.ravel()).reshape(c.shape)
+        y, it = cg(lambda v: coarse_apply(self.A, v, self.blocking), c,
+                   self.coarse_tol, self.coarse_maxiter)
+        self.coarse_iters.append(it)
+        return y
+
+    def R(self, v):
+        return restrict(self.phi, v, self.blocking)
+
+    def P(self, c):
+        return prolong(self.phi, c, self.blocking)
+
+    def Q(self, v):
+        return self.P(self.coarse_solve(self.R(v)))
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    iterations: int
+    true_residual: float
+    history: list
+    invariants: list = field(default_factory=list)
+
+
+def adef2(apply_H, b, defl: DeflationSpace, tol: float, maxiter: int = 10000,
+          mirs_iter: int = 7, mirs_shift: float = 1.0, flexible: bool = True,
+          x_guess=None, track_invariants: bool = False, apply_H_sloppy=None):
+    """A-DEF2 preconditioned CG (Fig. pcg_general, Table algos row A-DEF2).
+
+    x_0 = Q b + P_R x (x = x_guess or 0), r_0 = b - H x_0,
+    y = M_1 r = z + Q (r - H z) with z = M_IRS r  (since P_R = 1 - Q H),
+    p_0 = y_0; per iteration w = H p, alpha = (r, y)/(p, w), x += alpha p,
+    r -= alpha w, y' = M_1 r, beta (flexible or standard), p = y' + beta p.
+    Stops when the recursive residual reaches ``tol``; returns the true residual.
+    ``apply_H_sloppy`` (default: ``apply_H``) is the operator inside M_1.
+    """
+    Hs = apply_H if apply_H_sloppy is None else apply_H_sloppy
+    Q = defl.Q
+    if x_guess is None:
+        x = Q(b)
+    else:
+        x = Q(b) + x_guess - Q(apply_H(x_guess))
+    r = b - apply_H(x)
+    bb = _n2(b)
+
+    def M1(res):
+        z = mirs(Hs, res, mirs_iter, mirs_shift)
+        return z + Q(res - Hs(z))
+
+    y = M1(r)
+    p = y.copy()
+    ry = _dot(r, y).real
+    hist = [np.sqrt(_n2(r) / bb)]
+    inv = []
+    it = 0
+    while hist[-1] > tol and it < maxiter:
+        w = apply_H(p)
+        alpha = ry / _dot(p, w).real
+        x = x + alpha * p
+        r = r - alpha * w
+        it += 1
+        hist.append(np.sqrt(_n2(r) / bb))
+        if track_invariants:
+            qr = Q(r)
+            inv.append((np.sqrt(_n2(qr) / _n2(r)), np.sqrt(_n2(apply_H(qr)) / _n2(r))))
+        if hist[-1] <= tol:
+            break
+        y_new = M1(r)
+        ry_new = _dot(r, y_new).real
+        if flexible:
+            beta = (ry_new - _dot(r, y).real) / ry
+        else:
+            beta = ry_new / ry
+        p = y_new + beta * p
+        y = y_new
+        ry = ry_new
+    true_res = np.sqrt(_n2(b - apply_H(x)) / bb)
+    return SolveResult(x, it, true_res, hist, inv)

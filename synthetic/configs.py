@@ -1,0 +1,72 @@
+"""Workload recipes: lattice shapes, operator parameters and seeds.
+
+The paper's measurements use RBC-UKQCD gauge configurations (48^3x96x24 and
+32^4, Sec. 6) which are not available here.  Seeded random links
+U = exp(i eps H) stand in for them; they are smoother than physical fields
+and carry no topology, so iteration counts differ from the paper's.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dims: tuple          # (Lx, Ly, Lz, Lt)
+    Ls: int
+    M5: float
+    b: float
+    c: float
+    mass: float
+    eps: float
+    block: tuple         # fine-block extents
+    nvec: int
+    tol: float
+    prec: str            # fine-operator storage precision
+    nrhs: int = 1
+    block2: tuple | None = None   # second blocking (on the coarse lattice)
+    nvec2: int = 0
+    seed: int = 0
+    antiperiodic_t: bool = False
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def gauge_seed(self) -> int:
+        return 1000 + self.seed
+
+    @property
+    def source_seed(self) -> int:
+        return 2000 + self.seed
+
+    @property
+    def subspace_seed(self) -> int:
+        return 3000 + self.seed
+
+    @property
+    def coarse_dims(self):
+        return tuple(d // bk for d, bk in zip(self.dims, self.block))
+
+
+WORKLOADS = {
+    # plain FP64, tiny; the oracle finishes it in seconds
+    "cfg1_8x8x8x8_ls8_shamir": Workload(
+        "cfg1_8x8x8x8_ls8_shamir", (8, 8, 8, 8), 8, 1.8, 1.0, 0.0, 0.01, 0.3,
+        (4, 4, 4, 4), 8, 1e-10, "f64", seed=1),
+    # FP32 fine operator, two-level HDCG
+    "cfg2_16x16x16x16_ls16_shamir": Workload(
+        "cfg2_16x16x16x16_ls16_shamir", (16, 16, 16, 16), 16, 1.8, 1.0, 0.0, 0.005, 0.35,
+        (4, 4, 4, 4), 24, 1e-8, "f32", seed=2),
+    # FP16 storage, Moebius
+    "cfg3_24x24x24x48_ls16_mobius": Workload(
+        "cfg3_24x24x24x48_ls16_mobius", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.002, 0.4,
+        (4, 4, 4, 4), 32, 1e-8, "f16", seed=3),
+    # batched: 12 spin-colour point sources
+    "cfg4_24x24x24x48_ls16_mobius_12rhs": Workload(
+        "cfg4_24x24x24x48_ls16_mobius_12rhs", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.002, 0.4,
+        (4, 4, 4, 4), 32, 1e-8, "f16", nrhs=12, seed=4),
+    # physical-point-like, three levels
+    "cfg5_32x32x32x64_ls16_mobius_3lvl": Workload(
+        "cfg5_32x32x32x64_ls16_mobius_3lvl", (32, 32, 32, 64), 16, 1.8, 1.5, 0.5, 0.001, 0.45,
+        (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=5),
+}
