@@ -1,0 +1,205 @@
+/*
+ * hdcg.h -- C ABI of the GB300 (sm_103a) hierarchically deflated CG library.
+ *
+ * The calls follow the statement of the problem in Boyle, "Hierarchically
+ * deflated conjugate gradient" (arXiv 1402.2585): a 4D lattice with a fifth
+ * dimension of extent Ls, an SU(3) gauge field, the domain-wall / Moebius
+ * parameters (M5, b, c, m), the red-black preconditioned Hermitian operator
+ * H = Mpc^dag Mpc (Sec. 4), a blocked deflation subspace (Sec. 2), the little
+ * Dirac operator A (Sec. 2, Sec. 5.1, Sec. 5.1.1) and the A-DEF2 solve
+ * (Fig. pcg_general, Table algos).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value: HDCG_OK (0) on success; HDCG_NOT_CONVERGED (+1) when a solve
+ *   stops at its iteration limit (x then holds the last iterate); a negative
+ *   HDCG_ERR_* code otherwise.  hdcg_last_error() gives a one-line reason.
+ *   A call that fails leaves the handle usable unless it reports
+ *   HDCG_ERR_CUDA (a CUDA error may poison the context).
+ * Lattice: extents (Lx, Ly, Lz, Lt) all even; site lex = x + Lx(y + Ly(z + Lz t));
+ *   parity (x+y+z+t) mod 2; checkerboard index cb = lex >> 1.  The solved system
+ *   lives on the odd checkerboard.  Ls must be a power of two between 2 and 32.
+ * Canonical fermion field ("odd field"): [cb][s][spin 4][colour 3] complex,
+ *   real and imaginary parts interleaved, element type given by a precision
+ *   code (HDCG_F64: double, HDCG_F32: float, HDCG_F16: IEEE half,
+ *   HDCG_BF16 / HDCG_BF16T: bfloat16).  Size (V/2) * Ls * 12 complex.
+ *   Gamma matrices: chiral basis, gamma5 = diag(1, 1, -1, -1).
+ * Canonical gauge field: [lex][mu = x, y, z, t][row 3][col 3] complex double;
+ *   U_mu(x) links x to x + mu.
+ * Canonical coarse vector: [coarse site][Nvec] complex; coarse sites are the
+ *   blocks in lexicographic order of their block coordinates.
+ * Canonical coarse operator: [coarse site a][l][j][k] complex double with
+ *   A[a][l][j][k] = <phi_j^a | H | phi_k^{a + delta_l}>,
+ *   l = (dx+1) + 3 (dy+1) + 9 (dz+1) + 27 (dt+1), delta in {-1, 0, 1}^4.
+ *   Along a coarse extent of 2 only delta in {0, +1} is stored (delta = -1
+ *   aliases +1), along an extent of 1 only delta = 0; other entries are zero.
+ * Pointers: device pointers on the handle's stream unless a call takes an
+ *   on_device flag (0 = host memory).  The caller owns every buffer it passes;
+ *   the handle owns the internal copies and work space it allocates.
+ *   Calls are asynchronous on the stream only where stated; the others
+ *   synchronise the stream before returning.
+ */
+#ifndef HDCG_H
+#define HDCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* precision codes: storage type; arithmetic is FP32 for 16/32-bit storage, FP64 for FP64 */
+#define HDCG_F64   0
+#define HDCG_F32   1
+#define HDCG_F16   2   /* IEEE half, round to nearest even */
+#define HDCG_BF16  3   /* bfloat16 (8-bit exponent, 7-bit mantissa), round to nearest even */
+#define HDCG_BF16T 4   /* bfloat16 by truncating the float32 word to its top 16 bits (Sec. 6.5) */
+
+/* return codes */
+#define HDCG_OK             0
+#define HDCG_NOT_CONVERGED  1
+#define HDCG_ERR_ARG       -1  /* invalid argument or unsupported size */
+#define HDCG_ERR_OOM       -2  /* device allocation failed */
+#define HDCG_ERR_CUDA      -3  /* a CUDA call failed */
+#define HDCG_ERR_NONFINITE -4  /* a residual or inner product became NaN/Inf */
+#define HDCG_ERR_BREAKDOWN -5  /* (p, Hp) <= 0 or (r, y) <= 0 in a Krylov step */
+#define HDCG_ERR_STATE     -7  /* prerequisite missing (no gauge field, no subspace, ...) */
+
+/* solver algorithms */
+#define HDCG_ALG_CG    0  /* plain CG on H (the red-black normal-equation baseline) */
+#define HDCG_ALG_ADEF2 1  /* A-DEF2: V_start = Qb + P_R x, M1 = P_R M_IRS + Q (Table algos) */
+
+typedef struct hdcg_ctx* hdcg_t;
+
+/* Create a lattice of extents dims[4] with fifth-dimension extent Ls.
+ * antiperiodic_t: 1 multiplies hops across the time boundary by -1.
+ * cuda_stream: cudaStream_t to run on (NULL = legacy default stream).
+ * Allocates only small index tables.  Errors: HDCG_ERR_ARG (odd or < 2 extent,
+ * Ls not a power of two in [2, 32]), HDCG_ERR_OOM, HDCG_ERR_CUDA. */
+int hdcg_create(hdcg_t* h, const int dims[4], int Ls, int antiperiodic_t, void* cuda_stream);
+
+/* Domain-wall / Moebius parameters (Sec. 4 operator; Shamir: b = 1, c = 0).
+ * D psi_s = D_W (K psi)_s + ((1 - P_s) psi)_s, K = b + c P_s,
+ * (P_s psi)_s = P_- psi_{s+1} + P_+ psi_{s-1}, psi_{Ls} -> -m psi_0, psi_{-1} -> -m psi_{Ls-1},
+ * D_W = (4 - M5) - Dh/2.  Errors: HDCG_ERR_ARG if M_ee is singular. */
+int hdcg_set_dwf(hdcg_t h, double M5, double b, double c, double mass);
+
+/* Upload the gauge field (canonical, complex double, host or device).  The
+ * library keeps its own copies in FP64, FP32 and 16-bit link layouts.  The
+ * links are reused across all Ls slices (Sec. 6.5).  Synchronous. */
+int hdcg_set_gauge(hdcg_t h, const void* U, int on_device);
+
+/* out = Mpc in (dagger = 0) or Mpc^dag in (dagger = 1) on odd fields, where
+ * Mpc = M_oo - M_oe M_ee^-1 M_eo (Sec. 4).  in/out: canonical odd fields of
+ * precision prec on the device, distinct buffers.  Asynchronous on the stream. */
+int hdcg_apply_mpc(hdcg_t h, const void* in, void* out, int dagger, int prec);
+
+/* out = H in = Mpc^dag Mpc in (Sec. 4).  If pHp is not NULL it receives
+ * (in, H in) = |Mpc in|^2 accumulated in FP64 (then the call synchronises). */
+int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp);
+
+/* ---------------------------------------------------------------------------
+ * Deflation subspace and little Dirac operator (Sec. 2, Sec. 5.1)
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int block[4];        /* block extents; each >= 4 and dividing the lattice extent */
+    int nvec;            /* number of subspace vectors, 1..64 */
+    int prec;            /* storage precision of the subspace: HDCG_F64, _F32 or _F16 */
+    int inv_steps;       /* inverse-iteration steps (each followed by block Gram-Schmidt) */
+    double inv_shift;    /* lambda_s: each step applies (H + lambda_s)^-1 */
+    double inv_tol;      /* relative residual of the CG in each step */
+    int inv_maxiter;     /* iteration cap of that CG */
+    uint64_t seed;       /* Gaussian start vectors: splitmix64 counter stream + Box-Muller */
+} hdcg_subspace_params;
+
+/* Build the subspace by inverse iteration on H from Gaussian noise, with block
+ * Gram-Schmidt (FP64 arithmetic) after each step (Sec. 2; inverse iteration
+ * as named in Sec. 1 and Sec. 5.2.1).  Synchronous. */
+int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p);
+
+/* Upload a subspace: phi canonical complex double [nvec][odd field], host or
+ * device.  It is block-orthonormalised again (FP64) before use unless
+ * already_orthonormal is 1.  Synchronous. */
+int hdcg_set_subspace(hdcg_t h, const int block[4], int nvec, int prec, const void* phi,
+                      int on_device, int already_orthonormal);
+
+/* Copy the subspace out (canonical complex double, host).  Synchronous. */
+int hdcg_get_subspace(hdcg_t h, void* phi_host);
+
+/* Assemble A = R H P by the Fourier trick of Sec. 5.1.1 (81 phased H applies
+ * per subspace vector, inverted one dimension at a time); prec is the storage
+ * precision of A (HDCG_F64, _F32 or _F16).  Synchronous. */
+int hdcg_build_coarse(hdcg_t h, int prec);
+
+/* Copy A out in the canonical layout (complex double, host).  Synchronous. */
+int hdcg_get_coarse(hdcg_t h, void* A_host);
+
+/* c = R v (c[b][k] = <phi_k^b, v>), v a canonical odd field of precision prec on
+ * the device, c a canonical coarse vector (complex double, device). */
+int hdcg_restrict(hdcg_t h, const void* v, int prec, void* c);
+/* v = P c = sum_k c[b(x)][k] phi_k(x); c complex double (device), v precision prec. */
+int hdcg_prolong(hdcg_t h, const void* c, void* v, int prec);
+/* y = A x on canonical coarse vectors (complex double, device). */
+int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
+
+/* ---------------------------------------------------------------------------
+ * Solve H x = b
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int algorithm;         /* HDCG_ALG_CG or HDCG_ALG_ADEF2 */
+    int outer_prec;        /* operator precision of the outer iteration (F64 or F32) */
+    int sloppy_prec;       /* precision of M_IRS and of the operator inside M1 */
+    int mirs_iter;         /* M_IRS CG iterations (Table optimised: 7) */
+    double mirs_shift;     /* M_IRS infra-red shift lambda (Table optimised: 1.0) */
+    double coarse_tol;     /* relative residual of the coarse CG (Table optimised: 0.04) */
+    int coarse_maxiter;
+    int flexible;          /* 1: flexible (Polak-Ribiere) beta; 0: standard PCG beta */
+    int maxiter;           /* outer iteration cap */
+    double reliable_delta; /* FP64 true-residual update when |r| falls by this factor */
+} hdcg_params;
+
+typedef struct {
+    int iterations;            /* outer iterations */
+    int coarse_iterations;     /* total coarse CG iterations */
+    int coarse_iterations_max; /* largest single coarse solve */
+    int n_mdagm_outer;         /* H applies in the outer precision */
+    int n_mdagm_sloppy;        /* H applies inside the preconditioner */
+    int n_mdagm_f64;           /* FP64 true-residual H applies */
+    int reliable_updates;
+    int status;                /* return code of the solve */
+    double true_residual;      /* |b - H x| / |b| in FP64 at exit (max over rhs) */
+    double seconds;            /* wall time of the solve */
+} hdcg_stats;
+
+/* Fill p with the defaults (A-DEF2, FP32 outer, FP32 sloppy, M_IRS(7, 1.0),
+ * coarse tol 0.04, flexible, reliable delta 0.1). */
+void hdcg_default_params(hdcg_params* p);
+
+/* Solve H x = b for nrhs right-hand sides to |b - H x| / |b| <= tol (true FP64
+ * residual).  b, x: nrhs consecutive canonical odd fields, complex double, on
+ * the device (on_device = 1) or host (0).  x is overwritten (zero start).
+ * HDCG_ALG_ADEF2 needs a subspace and a coarse operator.  Synchronous. */
+int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p,
+               hdcg_stats* st, int on_device);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation
+ * ------------------------------------------------------------------------- */
+/* Enable (1) / disable (0) CUDA-event timing of every fine-operator hop launch. */
+int hdcg_set_profiling(hdcg_t h, int on);
+/* Launch count, summed device time (ms) and algorithmic bytes of the fine
+ * hop kernels recorded since profiling was enabled, per storage precision
+ * (prec).  Synchronises the stream. */
+int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes);
+/* Count of library kernel launches issued on the handle since creation. */
+long long hdcg_launch_count(hdcg_t h);
+
+const char* hdcg_last_error(hdcg_t h);
+void hdcg_destroy(hdcg_t h);
+int hdcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDCG_H */

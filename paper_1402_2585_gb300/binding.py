@@ -1,0 +1,231 @@
+"""ctypes binding of libhdcg with the C ABI's names (argument marshalling only).
+
+Buffers may be torch tensors on the GPU (passed as device pointers) or numpy
+arrays / torch CPU tensors (host pointers, for the calls that accept host
+memory).  Complex data is passed as interleaved real/imaginary parts; the
+binding never computes anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+F64, F32, F16, BF16, BF16T = 0, 1, 2, 3, 4
+PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "bf16t": BF16T}
+ALG_CG, ALG_ADEF2 = 0, 1
+_ERRORS = {1: "not converged", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
+           -4: "non-finite value", -5: "Krylov breakdown", -7: "missing prerequisite"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libhdcg.so")
+
+
+class HdcgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hdcg error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class SubspaceParams(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("prec", ctypes.c_int),
+                ("inv_steps", ctypes.c_int), ("inv_shift", ctypes.c_double), ("inv_tol", ctypes.c_double),
+                ("inv_maxiter", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("algorithm", ctypes.c_int), ("outer_prec", ctypes.c_int), ("sloppy_prec", ctypes.c_int),
+                ("mirs_iter", ctypes.c_int), ("mirs_shift", ctypes.c_double), ("coarse_tol", ctypes.c_double),
+                ("coarse_maxiter", ctypes.c_int), ("flexible", ctypes.c_int), ("maxiter", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("coarse_iterations", ctypes.c_int),
+                ("coarse_iterations_max", ctypes.c_int), ("n_mdagm_outer", ctypes.c_int),
+                ("n_mdagm_sloppy", ctypes.c_int), ("n_mdagm_f64", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "hdcg_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), _I, _I, _P]),
+    "hdcg_set_dwf": (_I, [_P, _D, _D, _D, _D]),
+    "hdcg_set_gauge": (_I, [_P, _P, _I]),
+    "hdcg_apply_mpc": (_I, [_P, _P, _P, _I, _I]),
+    "hdcg_apply_mdagm": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "hdcg_build_subspace": (_I, [_P, ctypes.POINTER(SubspaceParams)]),
+    "hdcg_set_subspace": (_I, [_P, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
+    "hdcg_get_subspace": (_I, [_P, _P]),
+    "hdcg_build_coarse": (_I, [_P, _I]),
+    "hdcg_get_coarse": (_I, [_P, _P]),
+    "hdcg_restrict": (_I, [_P, _P, _I, _P]),
+    "hdcg_prolong": (_I, [_P, _P, _P, _I]),
+    "hdcg_coarse_apply": (_I, [_P, _P, _P]),
+    "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
+    "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
+    "hdcg_set_profiling": (_I, [_P, _I]),
+    "hdcg_get_hop_profile": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                                  ctypes.POINTER(_D)]),
+    "hdcg_launch_count": (ctypes.c_longlong, [_P]),
+    "hdcg_last_error": (ctypes.c_char_p, [_P]),
+    "hdcg_destroy": (None, [_P]),
+    "hdcg_version": (_I, []),
+}
+
+
+def lib():
+    """Load libhdcg.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(paper_1402_2585_gb300/build.py); there is no CPU fallback")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _on_device(x) -> int:
+    return int(bool(getattr(x, "is_cuda", False)))
+
+
+class Hdcg:
+    """One handle of the C library; methods mirror the hdcg_* calls."""
+
+    def __init__(self, dims, Ls, antiperiodic_t=False, stream=None):
+        self._L = lib()
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        st = ctypes.c_void_p(int(stream)) if stream is not None else None
+        rc = self._L.hdcg_create(ctypes.byref(h), d, int(Ls), int(bool(antiperiodic_t)), st)
+        if rc != 0:
+            raise HdcgError(rc, "hdcg_create failed")
+        self.h = h
+        self.dims = tuple(int(v) for v in dims)
+        self.Ls = int(Ls)
+
+    # -- helpers ------------------------------------------------------------
+    def _check(self, rc, allow_not_converged=False):
+        if rc == 0 or (allow_not_converged and rc == 1):
+            return rc
+        raise HdcgError(rc, self._L.hdcg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.hdcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- operator -----------------------------------------------------------
+    def set_dwf(self, M5, b, c, mass):
+        return self._check(self._L.hdcg_set_dwf(self.h, M5, b, c, mass))
+
+    def set_gauge(self, U):
+        return self._check(self._L.hdcg_set_gauge(self.h, _ptr(U), _on_device(U)))
+
+    def apply_mpc(self, inp, out, dagger=False, prec=F32):
+        return self._check(self._L.hdcg_apply_mpc(self.h, _ptr(inp), _ptr(out), int(bool(dagger)), prec))
+
+    def apply_mdagm(self, inp, out, prec=F32, want_pHp=False):
+        v = ctypes.c_double(0.0)
+        self._check(self._L.hdcg_apply_mdagm(self.h, _ptr(inp), _ptr(out), prec,
+                                             ctypes.byref(v) if want_pHp else None))
+        return v.value if want_pHp else None
+
+    # -- subspace and coarse operator -----------------------------------------
+    def build_subspace(self, block, nvec, prec=F32, inv_steps=3, inv_shift=0.0, inv_tol=1e-4,
+                       inv_maxiter=20000, seed=0):
+        p = SubspaceParams((ctypes.c_int * 4)(*block), nvec, prec, inv_steps, inv_shift, inv_tol,
+                           inv_maxiter, seed)
+        return self._check(self._L.hdcg_build_subspace(self.h, ctypes.byref(p)))
+
+    def set_subspace(self, block, phi, prec=F32, already_orthonormal=False):
+        nvec = int(phi.shape[0])
+        return self._check(self._L.hdcg_set_subspace(self.h, (ctypes.c_int * 4)(*block), nvec, prec, _ptr(phi),
+                                                     _on_device(phi), int(bool(already_orthonormal))))
+
+    def get_subspace(self, out):
+        return self._check(self._L.hdcg_get_subspace(self.h, _ptr(out)))
+
+    def build_coarse(self, prec=F32):
+        return self._check(self._L.hdcg_build_coarse(self.h, prec))
+
+    def get_coarse(self, out):
+        return self._check(self._L.hdcg_get_coarse(self.h, _ptr(out)))
+
+    def restrict(self, v, prec, c_out):
+        return self._check(self._L.hdcg_restrict(self.h, _ptr(v), prec, _ptr(c_out)))
+
+    def prolong(self, c_in, v_out, prec):
+        return self._check(self._L.hdcg_prolong(self.h, _ptr(c_in), _ptr(v_out), prec))
+
+    def coarse_apply(self, x, y):
+        return self._check(self._L.hdcg_coarse_apply(self.h, _ptr(x), _ptr(y)))
+
+    # -- solve ----------------------------------------------------------------
+    @staticmethod
+    def default_params(**kw) -> SolveParams:
+        p = SolveParams()
+        lib().hdcg_default_params(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    def solve(self, b, x, tol, params: SolveParams | None = None, nrhs=1):
+        st = SolveStats()
+        p = params if params is not None else self.default_params()
+        rc = self._L.hdcg_solve(self.h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(p), ctypes.byref(st),
+                                _on_device(b))
+        self._check(rc, allow_not_converged=True)
+        return st
+
+    # -- instrumentation ------------------------------------------------------
+    def set_profiling(self, on):
+        return self._check(self._L.hdcg_set_profiling(self.h, int(bool(on))))
+
+    def get_hop_profile(self, prec):
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        self._check(self._L.hdcg_get_hop_profile(self.h, prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return n.value, ms.value, by.value
+
+    def launch_count(self):
+        return int(self._L.hdcg_launch_count(self.h))

@@ -1,0 +1,66 @@
+// Blocked subspace and little Dirac operator state (coarse.cu).
+#pragma once
+
+#include "blas.cuh"
+
+namespace hdcg {
+
+struct Subspace {
+  int block[4] = {0, 0, 0, 0};
+  int cdims[4] = {0, 0, 0, 0};
+  size_t Vc = 0;            // coarse sites (blocks)
+  int nvec = 0;
+  int prec = HDCG_F32;      // storage precision of the vectors
+  int spb = 0;              // odd 4D sites per block
+  DevMem vecs;              // nvec fields, chunked layout, precision prec
+  DevMem block_of_site;     // int32 [n4]: block of each odd cb site
+  DevMem block_sites;       // int32 [Vc][spb]: odd cb sites of each block, ascending
+  DevMem block_coords;      // int32 [Vc][4]
+  size_t vec_bytes(const Ctx& c) const { return c.field_bytes(prec); }
+  uint4* vec(const Ctx& c, int k) const {
+    return reinterpret_cast<uint4*>(reinterpret_cast<char*>(vecs.p) + (size_t)k * vec_bytes(c));
+  }
+};
+
+struct Coarse {
+  int prec = HDCG_F32;      // storage of A (F64, F32 or F16); vectors: F64 if A is F64 else F32
+  int nvec = 0;
+  size_t Vc = 0;
+  DevMem A;                 // [Vc][81][k][j] complex (blocks stored transposed)
+  DevMem cnbr;              // int32 [Vc][81]: coarse neighbour a + delta_l
+  DevMem work;              // coarse CG vectors
+  DevMem ctl;               // coarse CG control block (doubles + ints)
+  DevMem qvec;              // restriction / coarse solution vectors of Q
+  int last_iters = 8;
+  int vec_prec() const { return prec == HDCG_F64 ? HDCG_F64 : HDCG_F32; }
+  size_t vec_bytes() const { return Vc * nvec * (vec_prec() == HDCG_F64 ? 16 : 8); }
+};
+
+// subspace geometry (host tables -> device)
+void subspace_init(Ctx& c, Subspace& s, const int block[4], int nvec, int prec);
+// Gaussian noise in every subspace vector (splitmix64 counter stream, Box-Muller),
+// drawn in canonical order [k][cb][s][spin][colour][re, im]
+void subspace_noise(Ctx& c, Subspace& s, uint64_t seed);
+// block orthonormalisation: two rounds of (block Gram matrix in FP64,
+// Cholesky G = R^dag R in FP64, Phi <- Phi R^-1)
+void block_orthonormalise(Ctx& c, Subspace& s);
+
+// c[b][k] = <phi_k^b, v>; c complex in coarse vector precision (vprec)
+void restrict_field(Ctx& c, const Subspace& s, const uint4* v, int vprec, void* cvec, int cprec);
+// out = (add ? add : 0) + sum_k c[b(x)][k] phi_k(x)
+void prolong_field(Ctx& c, const Subspace& s, const void* cvec, int cprec, uint4* out, int oprec,
+                   const uint4* add);
+
+// little Dirac operator
+void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec);
+void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec);
+// y = A x (+ |<x, y>| real part into red_result if not null); vectors in A.vec_prec()
+void coarse_apply(Ctx& c, const Coarse& A, const void* x, void* y, double* xAx);
+// coarse CG to relative residual tol from zero; returns iterations
+int coarse_cg(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter);
+// coarse vectors: complex double <-> coarse vector precision (n complex)
+void cvec_convert(Ctx& c, const void* in, int pin, void* out, int pout, size_t n);
+// canonical export of A (complex double [Vc][81][j][k], host)
+void coarse_export(Ctx& c, const Coarse& A, void* host);
+
+}  // namespace hdcg

@@ -1,0 +1,161 @@
+// Internal state of one HDCG handle (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hdcg.h"
+
+namespace hdcg {
+
+// status propagation ----------------------------------------------------------
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define HDCG_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::hdcg::Error{HDCG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define HDCG_REQUIRE(cond, code, msg)                                   \
+  do {                                                                  \
+    if (!(cond)) throw ::hdcg::Error{(code), std::string(msg)};        \
+  } while (0)
+
+inline bool is_16bit(int prec) { return prec == HDCG_F16 || prec == HDCG_BF16 || prec == HDCG_BF16T; }
+inline size_t bytes_per_real(int prec) { return prec == HDCG_F64 ? 8 : prec == HDCG_F32 ? 4 : 2; }
+inline int link_slot(int prec) { return prec == HDCG_BF16T ? HDCG_BF16 : prec; }
+
+// device memory owned by the handle ----------------------------------------------
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t n) {
+    if (bytes >= n && p) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw Error{HDCG_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+    }
+    bytes = n;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// a fine odd/even field in the internal chunked layout
+struct FieldRef {
+  uint4* p;
+  int prec;
+};
+
+// Moebius coefficients of the s-direction operators (site independent, real)
+struct DwfCoeffs {
+  double M5 = 1.8, b = 1.0, c = 0.0, mass = 0.01;
+  double alpha = 0, beta = 0;   // M_ee = alpha + beta P_s
+  double minv_norm = 0;         // M_ee^-1 = minv_norm * sum_{k<Ls} r^k P_s^k
+  double minv_r = 0;            // r = -beta / alpha
+  double rpow[6] = {0, 0, 0, 0, 0, 0};  // r^(2^j)
+};
+
+// kernel-time profile of the fine hop kernels, per storage precision
+struct HopProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> pending;  // (start, stop) pairs, recorded on the stream
+  std::vector<int> pending_prec;
+  long long launches[5] = {0, 0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};
+  double bytes[5] = {0, 0, 0, 0, 0};
+};
+
+struct Ctx;
+struct Subspace;
+struct Coarse;
+
+struct Ctx {
+  int dims[4] = {0, 0, 0, 0};
+  int Ls = 0, lslog2 = 0;
+  int apbc = 0;
+  cudaStream_t stream = nullptr;
+  size_t V = 0, n4 = 0, n5 = 0;     // 4D volume, sites per parity, 5D sites per parity
+  bool have_gauge = false, have_dwf = false;
+  DwfCoeffs co;
+
+  DevMem nbr[2];          // int32 [n4][8]: neighbour cb index of output site x (parity p)
+  DevMem links[4][2];     // per link slot (F64, F32, F16, BF16) and output parity
+  DevMem scratch_f[5][20]; // work fields per precision (slot roles: solver.cu)
+  DevMem red_partials, red_ticket, scalars;
+  DevMem canon_in, canon_out;  // canonical <-> internal staging
+
+  Subspace* sub = nullptr;
+  Coarse* coarse = nullptr;
+
+  HopProfile prof;
+  long long launches = 0;
+  std::string err;
+
+  size_t field_bytes(int prec) const { return n5 * 24 * bytes_per_real(prec); }
+  uint4* scratch(int prec, int i) {
+    scratch_f[prec][i].ensure(field_bytes(prec));
+    return scratch_f[prec][i].as<uint4>();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// fine operator (dwf.cu)
+// ---------------------------------------------------------------------------
+enum HopPass { PASS_A = 0, PASS_B = 1, PASS_C = 2, PASS_D = 3 };
+// Epilogue of pass D: out = sD * (M_oo^dag in2 - 1/4 K^dag Dh^dag in) + lam * extra
+struct HopEpi {
+  double sD = 1.0;
+  double lam = 0.0;
+  const uint4* extra = nullptr;
+};
+
+void dwf_setup_tables(Ctx& c);
+void dwf_upload_gauge(Ctx& c, const void* U, bool on_device);
+void dwf_set_coeffs(Ctx& c, double M5, double b, double c_, double mass);
+// one hop pass; red (may be null) receives |out|^2 (FP64)
+void launch_hop(Ctx& c, int pass, int prec, const uint4* in, const uint4* in2, uint4* out,
+                const HopEpi& epi, double* red_result, int accumulate);
+// out = Mpc in or Mpc^dag in (uses scratch slot 0)
+void apply_mpc(Ctx& c, int prec, const uint4* in, uint4* out, int dagger, double* mpc_norm2);
+// out = sD * H in + lam * extra; mpc_norm2 (device double, may be null) gets |Mpc in|^2
+void apply_mdagm(Ctx& c, int prec, const uint4* in, uint4* out, double* mpc_norm2,
+                 double sD = 1.0, double lam = 0.0, const uint4* extra = nullptr);
+
+// ---------------------------------------------------------------------------
+// fields and BLAS-1 (blas.cu); all reductions accumulate in FP64
+// ---------------------------------------------------------------------------
+void canon_to_internal(Ctx& c, const void* canon, int canon_prec, uint4* out, int prec,
+                       size_t nfields = 1);
+void internal_to_canon(Ctx& c, const uint4* in, int prec, void* canon, int canon_prec,
+                       size_t nfields = 1);
+void convert_field(Ctx& c, const uint4* in, int pin, uint4* out, int pout, size_t nfields = 1);
+void zero_field(Ctx& c, uint4* f, int prec, size_t nfields = 1);
+// result[0] = |a|^2
+void norm2(Ctx& c, const uint4* a, int prec, size_t n_reals, double* result);
+// result[0:2] = <a, b> (complex)
+void cdot(Ctx& c, const uint4* a, const uint4* b, int prec, size_t n_reals, double* result);
+
+struct Scalars;  // device scalar block used by the solvers (solver.cu)
+
+}  // namespace hdcg

@@ -1,0 +1,340 @@
+// Krylov solvers of the HDCG library (Boyle, arXiv 1402.2585).
+//
+//  * cg_fixed / cg_to_tol: CG on (H + shift) in one storage precision; with a
+//    fixed iteration count and zero start this is the infra-red shifted
+//    smoother M_IRS(H, N, lambda) of Sec. 4.3.
+//  * apply_M1: the A-DEF2 preconditioner M1 = P_R M_IRS + Q of Table algos,
+//    evaluated as y = z + Q (r - H z), z = M_IRS r (P_R = 1 - Q H), with
+//    Q = P A^-1 R (Sec. 2) and the coarse CG stopped at a relative residual
+//    (Table optimised: 0.04).
+//  * solve_one: the generalised preconditioned CG of Fig. pcg_general with the
+//    A-DEF2 row (V_start = Q b, M2 = M3 = 1) or plain CG (M1 = 1).  Flexible
+//    beta is the Polak-Ribiere form (r_{k+1}, y_{k+1} - y_k) / (r_k, y_k)
+//    (reading of the flexible CG the paper cites).  The outer recursion runs
+//    in the outer precision; the solution accumulates in FP64 and the true
+//    residual b - H x is recomputed with the FP64 operator whenever |r| has
+//    fallen by reliable_delta, and at convergence (reliable updates).
+// All inner products are FP64 device scalars; alpha and beta are formed on
+// the device.  The host reads two scalars per outer iteration to decide on
+// reliable updates and termination.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "coarse.cuh"
+
+namespace hdcg {
+
+// scratch slot roles (per precision): see header comment of this file
+enum {
+  SL_XLO = 3, SL_R = 4, SL_P = 5, SL_W = 6, SL_Y = 7, SL_YN = 8,
+  SL_RS = 9, SL_Z = 10, SL_MRES = 11, SL_MP = 12, SL_MW = 13, SL_T = 14,
+  SL_XHI = 15, SL_B = 16, SL_R64 = 17, SL_CGB = 18, SL_CGX = 19
+};
+// device scalar slots (doubles)
+enum {
+  D_PW = 0, D_RR = 1, D_RY = 2, D_RYN = 3 /* 2 */, D_BB = 6, D_TMP = 7,
+  D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27
+};
+
+static double* dsc(Ctx& c, int slot) { return c.scalars.as<double>() + slot; }
+
+static void read_scalars(Ctx& c, int slot, int n, double* h) {
+  HDCG_CUDA(cudaMemcpyAsync(h, dsc(c, slot), n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+static void copy_scalar(Ctx& c, int dst, int src) {
+  HDCG_CUDA(cudaMemcpyAsync(dsc(c, dst), dsc(c, src), sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+}
+
+static void copy_field(Ctx& c, int prec, const uint4* in, uint4* out) {
+  HDCG_CUDA(cudaMemcpyAsync(out, in, c.field_bytes(prec), cudaMemcpyDeviceToDevice, c.stream));
+}
+
+// ---------------------------------------------------------------------------
+// CG on (H + shift) in one precision, zero start.
+// niter_fixed > 0: exactly that many iterations (M_IRS); otherwise iterate to
+// |r| <= tol |b| (checked on the host every iteration).
+// ---------------------------------------------------------------------------
+static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, int niter_fixed, double tol,
+                      int maxiter, int* n_mdagm) {
+  uint4* res = c.scratch(prec, SL_MRES);
+  uint4* p = c.scratch(prec, SL_MP);
+  uint4* w = c.scratch(prec, SL_MW);
+  zero_field(c, x, prec);
+  copy_field(c, prec, b, res);
+  copy_field(c, prec, b, p);
+  norm2(c, b, prec, 0, dsc(c, D_MRR));
+  copy_scalar(c, D_MPP, D_MRR);
+  double bb = 0.0;
+  if (niter_fixed <= 0) {
+    read_scalars(c, D_MRR, 1, &bb);
+    if (bb == 0.0) return 0;
+  }
+  const int nit = niter_fixed > 0 ? niter_fixed : maxiter;
+  int it = 0;
+  for (; it < nit; ++it) {
+    const int par = it & 1;
+    apply_mdagm(c, prec, p, w, dsc(c, D_MPW), 1.0, shift, shift != 0.0 ? p : nullptr);
+    if (n_mdagm) ++*n_mdagm;
+    ScalarRef al;
+    al.num = dsc(c, D_MRR + par);
+    al.den0 = dsc(c, D_MPW);
+    al.den1 = dsc(c, D_MPP);
+    al.lam = shift;
+    update_xr(c, prec, x, prec, p, res, w, al, 1, dsc(c, D_MRR + (par ^ 1)));
+    if (niter_fixed <= 0) {
+      double rr = 0.0;
+      read_scalars(c, D_MRR + (par ^ 1), 1, &rr);
+      HDCG_REQUIRE(std::isfinite(rr), HDCG_ERR_NONFINITE, "non-finite residual in CG");
+      if (rr <= tol * tol * bb) {
+        ++it;
+        break;
+      }
+    } else if (it == nit - 1) {
+      break;
+    }
+    ScalarRef be;
+    be.num = dsc(c, D_MRR + (par ^ 1));
+    be.den0 = dsc(c, D_MRR + par);
+    update_p(c, prec, p, res, be, dsc(c, D_MPP));
+  }
+  return niter_fixed > 0 ? nit : it;
+}
+
+// ---------------------------------------------------------------------------
+// Q t = P A^-1 R t (+ add) in the sloppy precision
+// ---------------------------------------------------------------------------
+static void apply_Q(Ctx& c, int sp, const uint4* t, uint4* out, const uint4* add, const hdcg_params& prm,
+                    hdcg_stats* st) {
+  Subspace& s = *c.sub;
+  Coarse& A = *c.coarse;
+  const int cp = A.vec_prec();
+  const size_t nc = A.Vc * A.nvec;
+  A.qvec.ensure(2 * nc * 16);
+  char* q0 = A.qvec.as<char>();
+  void* cin = q0;
+  void* cout = q0 + nc * 16;
+  restrict_field(c, s, t, sp, cin, cp);
+  const int it = coarse_cg(c, A, cin, cout, prm.coarse_tol, prm.coarse_maxiter);
+  if (st) {
+    st->coarse_iterations += it;
+    if (it > st->coarse_iterations_max) st->coarse_iterations_max = it;
+  }
+  prolong_field(c, s, cout, cp, out, sp, add);
+}
+
+// y = M1 r in precision op (A-DEF2) ; r in op
+static void apply_M1(Ctx& c, int op, int sp, const uint4* r, uint4* y, const hdcg_params& prm, hdcg_stats* st) {
+  const uint4* rs = r;
+  if (sp != op) {
+    uint4* t = c.scratch(sp, SL_RS);
+    convert_field(c, r, op, t, sp);
+    rs = t;
+  }
+  uint4* z = c.scratch(sp, SL_Z);
+  int nm = 0;
+  cg_shifted(c, sp, rs, z, prm.mirs_shift, prm.mirs_iter, 0.0, prm.mirs_iter, &nm);
+  uint4* t = c.scratch(sp, SL_T);
+  apply_mdagm(c, sp, z, t, nullptr, -1.0, 1.0, rs);  // t = r - H z
+  ++nm;
+  if (st) st->n_mdagm_sloppy += nm;
+  if (sp == op) {
+    apply_Q(c, sp, t, y, z, prm, st);
+  } else {
+    uint4* ys = c.scratch(sp, SL_MRES);
+    apply_Q(c, sp, t, ys, z, prm, st);
+    convert_field(c, ys, sp, y, op);
+  }
+}
+
+// x_hi (FP64) = Q b
+static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdcg_params& prm, hdcg_stats* st) {
+  uint4* bs = c.scratch(sp, SL_RS);
+  convert_field(c, b64, HDCG_F64, bs, sp);
+  uint4* x0 = c.scratch(sp, SL_T);
+  apply_Q(c, sp, bs, x0, nullptr, prm, st);
+  convert_field(c, x0, sp, xhi, HDCG_F64);
+}
+
+// r64 = b - H64 x_hi; returns |r64|^2 (host), r (op) = r64
+static double true_residual(Ctx& c, int op, const uint4* b64, const uint4* xhi, uint4* r, hdcg_stats* st) {
+  uint4* r64 = c.scratch(HDCG_F64, SL_R64);
+  apply_mdagm(c, HDCG_F64, xhi, r64, nullptr, -1.0, 1.0, b64);
+  if (st) ++st->n_mdagm_f64;
+  norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR));
+  if (op != HDCG_F64) convert_field(c, r64, HDCG_F64, r, op);
+  else copy_field(c, HDCG_F64, r64, r);
+  double rr = 0.0;
+  read_scalars(c, D_RR, 1, &rr);
+  return rr;
+}
+
+// one right-hand side: b64, x64 internal FP64 fields
+static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdcg_params& prm, hdcg_stats* st) {
+  const int op = prm.outer_prec, sp = prm.sloppy_prec;
+  const bool adef2 = prm.algorithm == HDCG_ALG_ADEF2;
+  HDCG_REQUIRE(op == HDCG_F64 || op == HDCG_F32, HDCG_ERR_ARG, "outer precision must be F64 or F32");
+  if (adef2) {
+    HDCG_REQUIRE(c.sub && c.coarse, HDCG_ERR_STATE, "A-DEF2 needs a subspace and a coarse operator");
+    HDCG_REQUIRE(sp >= HDCG_F64 && sp <= HDCG_BF16T, HDCG_ERR_ARG, "bad sloppy precision");
+  }
+  uint4* xlo = c.scratch(op, SL_XLO);
+  uint4* r = c.scratch(op, SL_R);
+  uint4* p = c.scratch(op, SL_P);
+  uint4* w = c.scratch(op, SL_W);
+  uint4* y = c.scratch(op, SL_Y);
+  uint4* yn = c.scratch(op, SL_YN);
+  uint4* xhi = x64;
+
+  norm2(c, b64, HDCG_F64, 0, dsc(c, D_BB));
+  double bb = 0.0;
+  read_scalars(c, D_BB, 1, &bb);
+  zero_field(c, xhi, HDCG_F64);
+  zero_field(c, xlo, op);
+  if (bb == 0.0) {
+    st->true_residual = 0.0;
+    return HDCG_OK;
+  }
+  const double stop = tol * tol * bb;
+  if (adef2) start_vector(c, sp, b64, xhi, prm, st);
+  double rr = true_residual(c, op, b64, xhi, r, st);
+  double rr_rel = rr;
+  if (rr <= stop) {
+    st->true_residual = std::sqrt(rr / bb);
+    return HDCG_OK;
+  }
+  // y_0 = M1 r_0, p_0 = y_0, ry = (r, y)
+  if (adef2) {
+    apply_M1(c, op, sp, r, y, prm, st);
+    copy_field(c, op, y, p);
+    redot2(c, op, r, y, nullptr, dsc(c, D_RYN));
+    copy_scalar(c, D_RY, D_RYN);
+  } else {
+    copy_field(c, op, r, p);
+    copy_scalar(c, D_RY, D_RR);
+  }
+  int it = 0;
+  int status = HDCG_NOT_CONVERGED;
+  while (it < prm.maxiter) {
+    apply_mdagm(c, op, p, w, dsc(c, D_PW));
+    ++st->n_mdagm_outer;
+    ScalarRef al;
+    al.num = dsc(c, D_RY);
+    al.den0 = dsc(c, D_PW);
+    update_xr(c, op, xlo, op, p, r, w, al, 1, dsc(c, D_RR));
+    ++it;
+    double h[2];
+    read_scalars(c, D_PW, 2, h);  // pw, rr
+    HDCG_REQUIRE(std::isfinite(h[0]) && std::isfinite(h[1]), HDCG_ERR_NONFINITE, "non-finite residual");
+    HDCG_REQUIRE(h[0] > 0.0, HDCG_ERR_BREAKDOWN, "(p, Hp) <= 0");
+    rr = h[1];
+    if (rr <= prm.reliable_delta * prm.reliable_delta * rr_rel || rr <= stop || it >= prm.maxiter) {
+      accum_hi(c, HDCG_F64, xhi, op, xlo);
+      rr = true_residual(c, op, b64, xhi, r, st);
+      rr_rel = rr;
+      ++st->reliable_updates;
+      if (rr <= stop) {
+        status = HDCG_OK;
+        break;
+      }
+    }
+    if (adef2) {
+      apply_M1(c, op, sp, r, yn, prm, st);
+      redot2(c, op, r, yn, y, dsc(c, D_RYN));  // (r, y_new), (r, y_old)
+      ScalarRef be;
+      be.num = dsc(c, D_RYN);
+      be.den0 = dsc(c, D_RY);
+      be.den1 = prm.flexible ? dsc(c, D_RYN + 1) : nullptr;
+      update_p(c, op, p, yn, be, nullptr);
+      copy_scalar(c, D_RY, D_RYN);
+      std::swap(y, yn);
+    } else {
+      ScalarRef be;
+      be.num = dsc(c, D_RR);
+      be.den0 = dsc(c, D_RY);
+      update_p(c, op, p, r, be, nullptr);
+      copy_scalar(c, D_RY, D_RR);
+    }
+  }
+  st->iterations += it;
+  const double tr = std::sqrt(rr / bb);
+  if (tr > st->true_residual) st->true_residual = tr;
+  return status;
+}
+
+int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_params& prm, hdcg_stats* st,
+          bool on_device) {
+  HDCG_REQUIRE(nrhs >= 1, HDCG_ERR_ARG, "nrhs >= 1");
+  HDCG_REQUIRE(tol > 0.0, HDCG_ERR_ARG, "tol > 0");
+  HDCG_REQUIRE(c.have_gauge && c.have_dwf, HDCG_ERR_STATE, "gauge field and DWF parameters required");
+  const auto t0 = std::chrono::steady_clock::now();
+  std::memset(st, 0, sizeof(*st));
+  const size_t canon = c.n5 * 12 * sizeof(double2);
+  DevMem hb;
+  uint4* b64 = c.scratch(HDCG_F64, SL_B);
+  uint4* x64 = c.scratch(HDCG_F64, SL_XHI);
+  int worst = HDCG_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    const char* bk = reinterpret_cast<const char*>(b) + k * canon;
+    char* xk = reinterpret_cast<char*>(x) + k * canon;
+    if (on_device) {
+      canon_to_internal(c, bk, HDCG_F64, b64, HDCG_F64);
+    } else {
+      c.canon_in.ensure(canon);
+      HDCG_CUDA(cudaMemcpyAsync(c.canon_in.p, bk, canon, cudaMemcpyHostToDevice, c.stream));
+      canon_to_internal(c, c.canon_in.p, HDCG_F64, b64, HDCG_F64);
+    }
+    const int rc = solve_one(c, b64, x64, tol, prm, st);
+    if (rc != HDCG_OK) worst = rc;
+    if (on_device) {
+      internal_to_canon(c, x64, HDCG_F64, xk, HDCG_F64);
+    } else {
+      c.canon_out.ensure(canon);
+      internal_to_canon(c, x64, HDCG_F64, c.canon_out.p, HDCG_F64);
+      HDCG_CUDA(cudaMemcpyAsync(xk, c.canon_out.p, canon, cudaMemcpyDeviceToHost, c.stream));
+    }
+  }
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  st->status = worst;
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// subspace by inverse iteration and the coarse operator
+// ---------------------------------------------------------------------------
+void build_subspace(Ctx& c, const hdcg_subspace_params& p) {
+  HDCG_REQUIRE(c.have_gauge && c.have_dwf, HDCG_ERR_STATE, "gauge field and DWF parameters required");
+  for (int mu = 0; mu < 4; ++mu)
+    HDCG_REQUIRE(p.block[mu] >= 4, HDCG_ERR_ARG, "block extents must be >= 4 (Sec. 5.1)");
+  if (!c.sub) c.sub = new Subspace();
+  Subspace& s = *c.sub;
+  subspace_init(c, s, p.block, p.nvec, p.prec);
+  subspace_noise(c, s, p.seed);
+  const int wp = p.prec == HDCG_F64 ? HDCG_F64 : HDCG_F32;
+  uint4* bk = c.scratch(wp, SL_CGB);
+  uint4* xk = c.scratch(wp, SL_CGX);
+  for (int step = 0; step < p.inv_steps; ++step) {
+    for (int k = 0; k < s.nvec; ++k) {
+      convert_field(c, s.vec(c, k), s.prec, bk, wp);
+      cg_shifted(c, wp, bk, xk, p.inv_shift, 0, p.inv_tol, p.inv_maxiter, nullptr);
+      convert_field(c, xk, wp, s.vec(c, k), s.prec);
+    }
+    block_orthonormalise(c, s);
+  }
+  if (p.inv_steps <= 0) block_orthonormalise(c, s);
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void build_coarse(Ctx& c, int prec) {
+  HDCG_REQUIRE(c.sub, HDCG_ERR_STATE, "no subspace");
+  HDCG_REQUIRE((prec == HDCG_F64) == (c.sub->prec == HDCG_F64), HDCG_ERR_ARG,
+               "the coarse operator is FP64 exactly when the subspace is FP64");
+  if (!c.coarse) c.coarse = new Coarse();
+  coarse_init(c, *c.coarse, *c.sub, prec);
+  coarse_assemble(c, *c.coarse, *c.sub, prec == HDCG_F64 ? HDCG_F64 : HDCG_F32);
+}
+
+}  // namespace hdcg

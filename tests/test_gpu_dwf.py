@@ -1,0 +1,101 @@
+"""Parity of the CUDA fine operator (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over the whole output): FP64 1e-12; FP32 1e-6 and
+FP16 storage 3e-3 (the operator-apply bars of the specification); BF16 with
+round-to-nearest 2e-2 and with truncation 4e-2 (8-bit mantissa: ~4e-3 per
+rounding, about eight roundings of input, links and intermediates).
+"""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle.dwf import DWF, norm2
+from paper_1402_2585_gb300 import BF16, BF16T, F16, F32, F64, Hdcg, HdcgError
+from tests.gpu_util import from_gpu, rel, to_gpu, torch_or_skip
+
+pytestmark = pytest.mark.gpu
+
+TOL = {F64: 1e-12, F32: 1e-6, F16: 3e-3, BF16: 2e-2, BF16T: 4e-2}
+
+CASES = {
+    "shamir_4x4x4x4_ls4": dict(dims=(4, 4, 4, 4), Ls=4, b=1.0, c=0.0, m=0.01, eps=0.3, apbc=False),
+    "mobius_8x4x4x6_ls8_apbc": dict(dims=(8, 4, 4, 6), Ls=8, b=1.5, c=0.5, m=0.002, eps=0.4, apbc=True),
+    "mobius_4x6x4x4_ls16": dict(dims=(4, 6, 4, 4), Ls=16, b=1.5, c=0.5, m=0.02, eps=0.45, apbc=False),
+    "shamir_2x2x2x2_ls2": dict(dims=(2, 2, 2, 2), Ls=2, b=1.0, c=0.0, m=0.1, eps=0.5, apbc=False),
+    "mobius_2x2x4x2_ls32": dict(dims=(2, 2, 4, 2), Ls=32, b=2.0, c=1.0, m=0.05, eps=0.5, apbc=True),
+}
+
+
+def _setup(case, seed=0):
+    torch = torch_or_skip()
+    p = CASES[case]
+    U = sy.gauge_field(p["dims"], p["eps"], 500 + seed)
+    d = DWF(p["dims"], p["Ls"], 1.8, p["b"], p["c"], p["m"], U, antiperiodic_t=p["apbc"])
+    h = Hdcg(p["dims"], p["Ls"], antiperiodic_t=p["apbc"], stream=torch.cuda.current_stream().cuda_stream)
+    h.set_dwf(1.8, p["b"], p["c"], p["m"])
+    h.set_gauge(torch.from_numpy(U).cuda())
+    return torch, d, h
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [F64, F32, F16, BF16, BF16T])
+def test_mpc_and_mdagm_parity(case, prec):
+    torch, d, h = _setup(case)
+    psi = sy.gaussian_fermion(d.lat.dims, d.Ls, 600)
+    x = to_gpu(psi, prec)
+    y = torch.empty_like(x)
+    for dagger, ref in ((False, d.mpc), (True, d.mpc_dag)):
+        h.apply_mpc(x, y, dagger=dagger, prec=prec)
+        err = rel(from_gpu(y), ref(psi))
+        assert err < TOL[prec], f"Mpc{'^dag' if dagger else ''} {case} prec {prec}: {err:.3e}"
+    pHp = h.apply_mdagm(x, y, prec=prec, want_pHp=True)
+    want = d.mdagm(psi)
+    err = rel(from_gpu(y), want)
+    assert err < TOL[prec], f"H {case} prec {prec}: {err:.3e}"
+    assert pHp == pytest.approx(norm2(d.mpc(psi)), rel=max(TOL[prec], 1e-12))
+
+
+def test_mdagm_full_size_fp32_16x16x16x16_ls16():
+    """The two-level workload's lattice (16^4 x 16, Shamir, m = 0.005) in FP32."""
+    w = sy.WORKLOADS["cfg2_16x16x16x16_ls16_shamir"]
+    torch = torch_or_skip()
+    U = sy.gauge_field(w.dims, w.eps, w.gauge_seed)
+    d = DWF(w.dims, w.Ls, w.M5, w.b, w.c, w.mass, U)
+    h = Hdcg(w.dims, w.Ls, stream=torch.cuda.current_stream().cuda_stream)
+    h.set_dwf(w.M5, w.b, w.c, w.mass)
+    h.set_gauge(torch.from_numpy(U).cuda())
+    psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
+    x = to_gpu(psi, F32)
+    y = torch.empty_like(x)
+    h.apply_mdagm(x, y, prec=F32)
+    assert rel(from_gpu(y), d.mdagm(psi)) < 1e-6
+
+
+def test_deterministic_and_hermitian():
+    torch, d, h = _setup("mobius_8x4x4x6_ls8_apbc")
+    u = to_gpu(sy.gaussian_fermion(d.lat.dims, d.Ls, 601), F64)
+    v = to_gpu(sy.gaussian_fermion(d.lat.dims, d.Ls, 602), F64)
+    hu, hv, hv2 = torch.empty_like(u), torch.empty_like(v), torch.empty_like(v)
+    p1 = h.apply_mdagm(v, hv, prec=F64, want_pHp=True)
+    p2 = h.apply_mdagm(v, hv2, prec=F64, want_pHp=True)
+    assert torch.equal(hv, hv2) and p1 == p2
+    h.apply_mdagm(u, hu, prec=F64)
+    a = np.vdot(from_gpu(u), from_gpu(hv))
+    b = np.conj(np.vdot(from_gpu(v), from_gpu(hu)))
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_argument_errors():
+    torch, d, h = _setup("shamir_4x4x4x4_ls4")
+    x = to_gpu(sy.gaussian_fermion(d.lat.dims, d.Ls, 603), F32)
+    with pytest.raises(HdcgError):
+        h.apply_mpc(x, x, prec=F32)          # aliasing in/out
+    with pytest.raises(HdcgError):
+        h.apply_mpc(x, torch.empty_like(x), prec=9)
+    with pytest.raises(HdcgError):
+        Hdcg((4, 4, 4, 3), 4)                 # odd extent
+    with pytest.raises(HdcgError):
+        Hdcg((4, 4, 4, 4), 12)                # Ls not a power of two
+    h2 = Hdcg((4, 4, 4, 4), 4)
+    with pytest.raises(HdcgError):
+        h2.apply_mpc(x, torch.empty_like(x), prec=F32)   # no gauge field yet
