@@ -1,0 +1,357 @@
+"""Benchmark: HDCG time-to-solution on one GB300 against plain red-black CG,
+with the fine Mpc^dag Mpc hop kernels' achieved bandwidth against the HBM roofline.
+
+One step = one full HDCG (A-DEF2) solve of H x = b to a true FP64 residual of
+``tol`` on the workload's lattice, inputs resident in HBM; subspace and coarse
+operator are built once before the timed region (the paper reports setup
+separately).  L2 is flushed (a 512 MiB write) before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME]
+Under torchrun (N > 1) every rank solves its own replica (independent seed);
+the timing is the max over ranks.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores (bounded sample, see ``cpu_sample``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as sy  # noqa: E402
+
+METRIC = "HDCG solve seconds vs plain CG at 1e-8 (1 GB300); fine Mpc†Mpc GB/s, %HBM peak"
+DEFAULT_WORKLOAD = "cfg2_16x16x16x16_ls16_shamir"
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+def oracle_h_seconds(w, reps=1):
+    """Seconds of one FP64 oracle H = Mpc^dag Mpc apply on the workload's full lattice."""
+    from oracle.dwf import DWF
+    U = sy.gauge_field(w.dims, w.eps, w.gauge_seed)
+    d = DWF(w.dims, w.Ls, w.M5, w.b, w.c, w.mass, U)
+    psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        d.mdagm(psi)
+        ts.append(time.perf_counter() - t0)
+    return min(ts)
+
+
+def cpu_sample_desc(w, n_h):
+    return (f"one FP64 oracle H apply on the full {'x'.join(map(str, w.dims))}x{w.Ls} lattice, "
+            f"scaled by the {n_h} fine H applies (outer + preconditioner + FP64 residual) of one HDCG solve "
+            "of this workload; coarse-grid work of the oracle not included")
+
+
+# H applies per HDCG solve of the default workload, recorded from the GPU arm's
+# solve statistics (a property of the algorithm on this input); used only to
+# scale the oracle's per-apply time in --impl reference, which runs no GPU code.
+H_APPLIES_PER_SOLVE = {DEFAULT_WORKLOAD: 420}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    n_h = H_APPLIES_PER_SOLVE.get(w.name, 420)
+    for _ in range(args.warmup):
+        oracle_h_seconds(w)
+    ts = [oracle_h_seconds(w) for _ in range(args.steps)]
+    per_h = statistics.mean(ts)
+    value = per_h * n_h
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_h * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "tol": w.tol},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": cpu_sample_desc(w, n_h)},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1402_2585_gb300 import ALG_ADEF2, ALG_CG, F64, Hdcg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    prec = PREC[w.prec]
+    sub_prec = prec if prec in (0, 1) else 2
+    coarse_prec = 0 if prec == 0 else (1 if prec == 1 else 2)
+    t_setup0 = time.perf_counter()
+    U = sy.gauge_field(w.dims, w.eps, w.gauge_seed + 100 * rank)
+    h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
+    h.set_dwf(w.M5, w.b, w.c, w.mass)
+    h.set_gauge(torch.from_numpy(U).to(dev))
+    t_sub0 = time.perf_counter()
+    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=3, inv_shift=0.0, inv_tol=1e-4, inv_maxiter=20000,
+                     seed=w.subspace_seed + rank)
+    t_sub = time.perf_counter() - t_sub0
+    t_c0 = time.perf_counter()
+    h.build_coarse(coarse_prec)
+    t_coarse = time.perf_counter() - t_c0
+    setup_s = time.perf_counter() - t_setup0
+
+    outer = 0 if prec == 0 else 1
+    prm = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000)
+    prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000)
+    b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, w.source_seed + rank)).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        h.solve(b, x, w.tol, prm)
+    barrier()
+
+    clk = ClockSampler(local)
+    clk.start()
+    h.set_profiling(True)
+    launches0 = h.launch_count()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(stream)
+        st = h.solve(b, x, w.tol, prm)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        stats.append(st.as_dict())
+    launches = h.launch_count() - launches0
+    n_hop, hop_ms, hop_bytes = h.get_hop_profile(outer)
+    phases = {k: v / args.steps for k, v in h.get_phase_profile().items()}
+    h.set_profiling(False)
+    clocks = clk.stop()
+
+    t_local = statistics.mean(times)
+    t_all = torch.tensor([t_local], device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    t_solve = float(t_all.item())
+
+    # plain red-black CG on the same GPU (same precision policy)
+    cg_times, cg_stats = [], None
+    for _ in range(max(1, min(2, args.steps))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cg_stats = h.solve(b, x, w.tol, prm_cg).as_dict()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        cg_times.append(e0.elapsed_time(e1) / 1e3)
+    t_cg = statistics.mean(cg_times)
+
+    # end to end through the public API with pinned host buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    e2e = []
+    for _ in range(max(1, min(3, args.steps))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h.solve(bh, xh, w.tol, prm)
+        e2e.append(time.perf_counter() - t0)
+    nbytes = bh.numel() * bh.element_size()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
+    s0 = stats[-1]
+    n_h = s0["n_mdagm_outer"] + s0["n_mdagm_sloppy"] + s0["n_mdagm_f64"]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        per_h = oracle_h_seconds(w)
+        cpu = {"value": per_h * n_h, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": cpu_sample_desc(w, n_h)}
+    line = {
+        "metric": METRIC, "value": t_solve, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "M5": w.M5, "b": w.b, "c": w.c,
+                   "mass": w.mass, "eps": w.eps, "block": list(w.block), "nvec": w.nvec, "tol": w.tol,
+                   "storage": w.prec, "rhs_per_gpu": 1, "l2": "flushed (512 MiB write) before each step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "hop_kernel (4 passes per H; FP32 storage)", "launches": n_hop,
+                     "avg_launch_us": hop_ms * 1e3 / max(1, n_hop), "peak_kind": f"{peak_kind} HBM copy"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(launches / max(1, args.steps)),
+        "clocks": clocks,
+        "plain_cg": {"seconds": t_cg, "iterations": cg_stats["iterations"],
+                     "true_residual": cg_stats["true_residual"]},
+        "speedup_vs_plain_cg": t_cg / t_solve if t_solve > 0 else None,
+        "hdcg": {"iterations": s0["iterations"], "coarse_iterations": s0["coarse_iterations"],
+                 "n_mdagm_outer": s0["n_mdagm_outer"], "n_mdagm_sloppy": s0["n_mdagm_sloppy"],
+                 "n_mdagm_f64": s0["n_mdagm_f64"], "reliable_updates": s0["reliable_updates"],
+                 "true_residual": s0["true_residual"]},
+        "phases_ms_per_solve": phases,
+        "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_apply_only(args, w):
+    """A small case for kernel profiling: ``args.apply_only`` H applies in the
+    workload's storage precision on device-resident canonical buffers (after
+    two warm-up applies); prints the mean time per apply."""
+    import torch
+
+    from paper_1402_2585_gb300 import Hdcg
+    prec = PREC[w.prec]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
+    h.set_dwf(w.M5, w.b, w.c, w.mass)
+    h.set_gauge(torch.from_numpy(sy.gauge_field(w.dims, w.eps, w.gauge_seed)).to(dev))
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}[prec]
+    psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
+    x = torch.view_as_real(torch.from_numpy(psi)).to(dt).to(dev).contiguous()
+    y = torch.empty_like(x)
+    for _ in range(2):
+        h.apply_mdagm(x, y, prec)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.apply_only):
+        h.apply_mdagm(x, y, prec)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"workload": w.name, "applies": args.apply_only,
+                      "ms_per_apply": e0.elapsed_time(e1) / args.apply_only}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sy.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", type=int, default=0,
+                    help="profiling case: run this many H applies only (no solve)")
+    args = ap.parse_args()
+    w = sy.WORKLOADS[args.workload]
+    if args.apply_only:
+        run_apply_only(args, w)
+    elif args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

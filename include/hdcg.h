@@ -192,6 +192,11 @@ int hdcg_set_profiling(hdcg_t h, int on);
  * hop kernels recorded since profiling was enabled, per storage precision
  * (prec).  Synchronises the stream. */
 int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes);
+/* Device time (ms, CUDA events) spent since profiling was enabled in each solve
+ * phase: ms[0] outer-precision H applies, ms[1] preconditioner H applies (M_IRS
+ * and r - H z), ms[2] FP64 true-residual H applies, ms[3] coarse CG, ms[4]
+ * restriction and prolongation, ms[5] whole solves.  Synchronises the stream. */
+int hdcg_get_phase_profile(hdcg_t h, double ms[6]);
 /* Count of library kernel launches issued on the handle since creation. */
 long long hdcg_launch_count(hdcg_t h);
 

@@ -78,6 +78,7 @@ _SIGS = {
     "hdcg_set_profiling": (_I, [_P, _I]),
     "hdcg_get_hop_profile": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                                   ctypes.POINTER(_D)]),
+    "hdcg_get_phase_profile": (_I, [_P, ctypes.POINTER(_D)]),
     "hdcg_launch_count": (ctypes.c_longlong, [_P]),
     "hdcg_last_error": (ctypes.c_char_p, [_P]),
     "hdcg_destroy": (None, [_P]),
@@ -226,6 +227,13 @@ class Hdcg:
         by = ctypes.c_double()
         self._check(self._L.hdcg_get_hop_profile(self.h, prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
         return n.value, ms.value, by.value
+
+    PHASES = ("h_outer", "h_sloppy", "h_f64", "coarse_cg", "restrict_prolong", "total")
+
+    def get_phase_profile(self):
+        ms = (ctypes.c_double * 6)()
+        self._check(self._L.hdcg_get_phase_profile(self.h, ms))
+        return dict(zip(self.PHASES, list(ms)))
 
     def launch_count(self):
         return int(self._L.hdcg_launch_count(self.h))

@@ -341,6 +341,36 @@ __global__ void k_scale_dev(const uint4* __restrict__ x, uint4* y, size_t n5, co
   store_spinor<S, R>(y, t, n5, v);
 }
 
+// out = s * in with s = sqrt(num / den) (inv: 1 / s), precisions may differ
+template <typename Si, typename So>
+__global__ void k_convert_scaled(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n5,
+                                 const double* num, const double* den, int inv) {
+  using Ri = typename Store<Si>::real;
+  using Ro = typename Store<So>::real;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n5) return;
+  const double q = (*den > 0.0 && *num > 0.0) ? *num / *den : 1.0;
+  double sc = sqrt(q);
+  if (inv) sc = 1.0 / sc;
+  Ri v[24];
+  load_spinor<Si, Ri>(in, t, n5, v);
+  Ro w[24];
+  const Ro s = (Ro)sc;
+#pragma unroll
+  for (int i = 0; i < 24; ++i) w[i] = (Ro)v[i] * s;
+  store_spinor<So, Ro>(out, t, n5, w);
+}
+
+void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, const double* num, const double* den,
+                    int inv) {
+  const unsigned g = blocks_for(c.n5);
+  DISPATCH_PREC(pin, Si, {
+    DISPATCH_PREC(pout, So, { k_convert_scaled<Si, So><<<g, 256, 0, c.stream>>>(in, out, c.n5, num, den, inv); });
+  });
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+}
+
 void update_xr(Ctx& c, int prec_x, uint4* x, int prec, const uint4* p, uint4* r, const uint4* w,
                ScalarRef alpha, int sign_x, double* rr_out) {
   const unsigned g = blocks_for(c.n5);

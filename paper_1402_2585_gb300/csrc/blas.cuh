@@ -55,6 +55,9 @@ void redot2(Ctx& c, int prec, const uint4* a, const uint4* b, const uint4* cc, d
 void accum_hi(Ctx& c, int prec_hi, uint4* hi, int prec_lo, uint4* lo);
 // y = a x + b y
 void axpby(Ctx& c, double a, int prec_x, const uint4* x, double b, int prec_y, uint4* y);
+// out = sqrt(num / den)^(inv ? -1 : 1) in, converting precision
+void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, const double* num, const double* den,
+                    int inv);
 // y = sqrt(num/den)^(inv ? -1 : 1) x
 void scale_dev(Ctx& c, int prec, const uint4* x, uint4* y, const double* num, const double* den, int inv);
 

@@ -31,6 +31,21 @@ static void resolve_profile(Ctx& c) {
   pr.pending_prec.clear();
 }
 
+static void resolve_phases(Ctx& c) {
+  auto& pp = c.phases;
+  if (pp.pending.empty()) return;
+  HDCG_CUDA(cudaEventSynchronize(pp.pending.back()));
+  for (size_t i = 0; i + 1 < pp.pending.size(); i += 2) {
+    float ms = 0.f;
+    HDCG_CUDA(cudaEventElapsedTime(&ms, pp.pending[i], pp.pending[i + 1]));
+    pp.ms[pp.phase[i / 2]] += ms;
+    cudaEventDestroy(pp.pending[i]);
+    cudaEventDestroy(pp.pending[i + 1]);
+  }
+  pp.pending.clear();
+  pp.phase.clear();
+}
+
 static void check_prec(int prec) {
   HDCG_REQUIRE(prec >= HDCG_F64 && prec <= HDCG_BF16T, HDCG_ERR_ARG, "unknown precision code");
 }
@@ -100,6 +115,7 @@ void hdcg_destroy(hdcg_t h) {
   Ctx* c = reinterpret_cast<Ctx*>(h);
   cudaStreamSynchronize(c->stream);
   for (auto e : c->prof.pending) cudaEventDestroy(e);
+  for (auto e : c->phases.pending) cudaEventDestroy(e);
   delete c->sub;
   delete c->coarse;
   delete c;
@@ -316,9 +332,21 @@ int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdc
   return HDCG_ERR_ARG;  // not reached
 }
 
+int hdcg_get_phase_profile(hdcg_t h, double ms[6]) {
+  HDCG_ENTRY(h, {
+    check_ptr(ms, "ms");
+    resolve_phases(c);
+    for (int i = 0; i < PH_N; ++i) ms[i] = c.phases.ms[i];
+  });
+  return HDCG_OK;
+}
+
 int hdcg_set_profiling(hdcg_t h, int on) {
   HDCG_ENTRY(h, {
     resolve_profile(c);
+    resolve_phases(c);
+    if (on)
+      for (int i = 0; i < PH_N; ++i) c.phases.ms[i] = 0;
     c.prof.on = on != 0;
     if (on) {
       for (int i = 0; i < 5; ++i) {

@@ -86,6 +86,14 @@ struct HopProfile {
   double bytes[5] = {0, 0, 0, 0, 0};
 };
 
+// solve-phase timing (CUDA events on the stream, resolved on request)
+enum Phase { PH_H_OUTER = 0, PH_H_SLOPPY = 1, PH_H_F64 = 2, PH_COARSE = 3, PH_TRANSFER = 4, PH_TOTAL = 5, PH_N = 6 };
+struct PhaseProfile {
+  std::vector<cudaEvent_t> pending;  // (start, stop) pairs
+  std::vector<int> phase;
+  double ms[PH_N] = {0, 0, 0, 0, 0, 0};
+};
+
 struct Ctx;
 struct Subspace;
 struct Coarse;
@@ -109,6 +117,7 @@ struct Ctx {
   Coarse* coarse = nullptr;
 
   HopProfile prof;
+  PhaseProfile phases;
   long long launches = 0;
   std::string err;
 
@@ -156,6 +165,27 @@ void norm2(Ctx& c, const uint4* a, int prec, size_t n_reals, double* result);
 // result[0:2] = <a, b> (complex)
 void cdot(Ctx& c, const uint4* a, const uint4* b, int prec, size_t n_reals, double* result);
 
-struct Scalars;  // device scalar block used by the solvers (solver.cu)
+// RAII phase timer: records (start, stop) events when profiling is on
+struct PhaseTimer {
+  Ctx& c;
+  int ph;
+  cudaEvent_t e0 = nullptr;
+  PhaseTimer(Ctx& c_, int ph_) : c(c_), ph(ph_) {
+    if (c.prof.on) {
+      cudaEventCreate(&e0);
+      cudaEventRecord(e0, c.stream);
+    }
+  }
+  ~PhaseTimer() {
+    if (e0) {
+      cudaEvent_t e1;
+      cudaEventCreate(&e1);
+      cudaEventRecord(e1, c.stream);
+      c.phases.pending.push_back(e0);
+      c.phases.pending.push_back(e1);
+      c.phases.phase.push_back(ph);
+    }
+  }
+};
 
 }  // namespace hdcg

@@ -130,13 +130,15 @@ __device__ __forceinline__ void apply_minv(R* v, int s, const HopArgs& a) {
 }
 
 // ------------------------------------------------------------------------------
-// spin projection (1 - sg gamma_mu) in the chiral basis:
-//   h = u - sg A_mu l,  result = (h, -sg B_mu h),  with A_mu, B_mu the 2x2
-//   off-diagonal blocks of gamma_mu (A_mu B_mu = 1).
+// spin projection (1 - SG gamma_MU) in the chiral basis:
+//   h = u - SG A_mu l,  result = (h, -SG B_mu h),  with A_mu, B_mu the 2x2
+//   off-diagonal blocks of gamma_mu (A_mu B_mu = 1):
+//   A_x l = (-i l1, -i l0), A_y l = (-l1, l0), A_z l = (-i l0, i l1), A_t l = (l0, l1)
+//   B_x h = (i h1, i h0),   B_y h = (h1, -h0), B_z h = (i h0, -i h1), B_t h = (h0, h1)
 // spinor reals index: (spin * 3 + colour) * 2 + {re, im}
 // ------------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void project(int mu, R sg, const R* p, R* h) {
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void project(const R* p, R* h) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R u0r = p[(0 * 3 + c) * 2], u0i = p[(0 * 3 + c) * 2 + 1];
@@ -144,49 +146,43 @@ __device__ __forceinline__ void project(int mu, R sg, const R* p, R* h) {
     const R l0r = p[(2 * 3 + c) * 2], l0i = p[(2 * 3 + c) * 2 + 1];
     const R l1r = p[(3 * 3 + c) * 2], l1i = p[(3 * 3 + c) * 2 + 1];
     R a0r, a0i, a1r, a1i;  // A_mu l
-    switch (mu) {
-      case 0:  // (-i l1, -i l0)
-        a0r = l1i; a0i = -l1r; a1r = l0i; a1i = -l0r; break;
-      case 1:  // (-l1, l0)
-        a0r = -l1r; a0i = -l1i; a1r = l0r; a1i = l0i; break;
-      case 2:  // (-i l0, i l1)
-        a0r = l0i; a0i = -l0r; a1r = -l1i; a1i = l1r; break;
-      default:  // (l0, l1)
-        a0r = l0r; a0i = l0i; a1r = l1r; a1i = l1i; break;
+    if (MU == 0) { a0r = l1i; a0i = -l1r; a1r = l0i; a1i = -l0r; }
+    else if (MU == 1) { a0r = -l1r; a0i = -l1i; a1r = l0r; a1i = l0i; }
+    else if (MU == 2) { a0r = l0i; a0i = -l0r; a1r = -l1i; a1i = l1r; }
+    else { a0r = l0r; a0i = l0i; a1r = l1r; a1i = l1i; }
+    if (SG > 0) {
+      h[(0 * 3 + c) * 2] = u0r - a0r; h[(0 * 3 + c) * 2 + 1] = u0i - a0i;
+      h[(1 * 3 + c) * 2] = u1r - a1r; h[(1 * 3 + c) * 2 + 1] = u1i - a1i;
+    } else {
+      h[(0 * 3 + c) * 2] = u0r + a0r; h[(0 * 3 + c) * 2 + 1] = u0i + a0i;
+      h[(1 * 3 + c) * 2] = u1r + a1r; h[(1 * 3 + c) * 2 + 1] = u1i + a1i;
     }
-    h[(0 * 3 + c) * 2] = u0r - sg * a0r;
-    h[(0 * 3 + c) * 2 + 1] = u0i - sg * a0i;
-    h[(1 * 3 + c) * 2] = u1r - sg * a1r;
-    h[(1 * 3 + c) * 2 + 1] = u1i - sg * a1i;
   }
 }
 
-// acc += (uh, -sg B_mu uh)
-template <typename R>
-__device__ __forceinline__ void reconstruct_add(int mu, R sg, const R* uh, R* acc) {
+// acc += (uh, -SG B_mu uh)
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void reconstruct_add(const R* uh, R* acc) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R h0r = uh[(0 * 3 + c) * 2], h0i = uh[(0 * 3 + c) * 2 + 1];
     const R h1r = uh[(1 * 3 + c) * 2], h1i = uh[(1 * 3 + c) * 2 + 1];
     R b0r, b0i, b1r, b1i;  // B_mu h
-    switch (mu) {
-      case 0:  // (i h1, i h0)
-        b0r = -h1i; b0i = h1r; b1r = -h0i; b1i = h0r; break;
-      case 1:  // (h1, -h0)
-        b0r = h1r; b0i = h1i; b1r = -h0r; b1i = -h0i; break;
-      case 2:  // (i h0, -i h1)
-        b0r = -h0i; b0i = h0r; b1r = h1i; b1i = -h1r; break;
-      default:  // (h0, h1)
-        b0r = h0r; b0i = h0i; b1r = h1r; b1i = h1i; break;
-    }
+    if (MU == 0) { b0r = -h1i; b0i = h1r; b1r = -h0i; b1i = h0r; }
+    else if (MU == 1) { b0r = h1r; b0i = h1i; b1r = -h0r; b1i = -h0i; }
+    else if (MU == 2) { b0r = -h0i; b0i = h0r; b1r = h1i; b1i = -h1r; }
+    else { b0r = h0r; b0i = h0i; b1r = h1r; b1i = h1i; }
     acc[(0 * 3 + c) * 2] += h0r;
     acc[(0 * 3 + c) * 2 + 1] += h0i;
     acc[(1 * 3 + c) * 2] += h1r;
     acc[(1 * 3 + c) * 2 + 1] += h1i;
-    acc[(2 * 3 + c) * 2] -= sg * b0r;
-    acc[(2 * 3 + c) * 2 + 1] -= sg * b0i;
-    acc[(3 * 3 + c) * 2] -= sg * b1r;
-    acc[(3 * 3 + c) * 2 + 1] -= sg * b1i;
+    if (SG > 0) {
+      acc[(2 * 3 + c) * 2] -= b0r; acc[(2 * 3 + c) * 2 + 1] -= b0i;
+      acc[(3 * 3 + c) * 2] -= b1r; acc[(3 * 3 + c) * 2 + 1] -= b1i;
+    } else {
+      acc[(2 * 3 + c) * 2] += b0r; acc[(2 * 3 + c) * 2 + 1] += b0i;
+      acc[(3 * 3 + c) * 2] += b1r; acc[(3 * 3 + c) * 2 + 1] += b1i;
+    }
   }
 }
 
@@ -217,6 +213,30 @@ template <> struct LinkOf<f16_t> { using T = __half2; };
 template <> struct LinkOf<bf16_t> { using T = __nv_bfloat162; };
 template <> struct LinkOf<bf16t_t> { using T = __nv_bfloat162; };
 
+// both hops along direction MU: forward (x + mu, projector 1 - SF g) and
+// backward (x - mu, projector 1 + SF g); the two neighbour spinors and links are
+// loaded before either is used so that their loads overlap.
+template <typename St, typename R, typename LT, int MU, int SF, bool KIN>
+__device__ __forceinline__ void hop_pair(const HopArgs& a, const int* nbv, const LT* lk, int s, R* acc) {
+  R pf[24], pb[24];
+  load_spinor<St, R>(a.in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
+  load_spinor<St, R>(a.in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
+  if (KIN) {
+    const R m = (R)a.mass;
+    apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
+    apply_lin<R, false>(pb, (R)a.b, (R)a.c, s, a.Ls, m);
+  }
+  R h[12], uh[12], U[18];
+  project<MU, SF>(pf, h);
+  load_link(lk + MU * 9, U);
+  su3_mul<R>(U, h, uh);
+  reconstruct_add<MU, SF>(uh, acc);
+  project<MU, -SF>(pb, h);
+  load_link(lk + (MU + 4) * 9, U);
+  su3_mul<R>(U, h, uh);
+  reconstruct_add<MU, -SF>(uh, acc);
+}
+
 // ------------------------------------------------------------------------------
 // one hop pass
 // ------------------------------------------------------------------------------
@@ -236,23 +256,17 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = 0;
 
-  const int* nb = a.nbr + x4 * 8;
+  // all eight neighbour indices at once (32 bytes, shared by the Ls lanes of a site)
+  const int4 nb0 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2);
+  const int4 nb1 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2 + 1);
+  const int nbv[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
   const LT* lk = reinterpret_cast<const LT*>(a.links) + x4 * 72;
-#pragma unroll 1
-  for (int dir = 0; dir < 8; ++dir) {
-    const int mu = dir & 3;
-    // Dh: forward (1 - g), backward (1 + g); Dh^dag flips both
-    const R sg = (dir < 4 ? R(1) : R(-1)) * (DAG ? R(-1) : R(1));
-    const size_t nsite5 = (size_t)__ldg(nb + dir) * a.Ls + s;
-    R psi[24];
-    load_spinor<St, R>(a.in, nsite5, a.n5, psi);
-    if (PASS == PASS_A && MOB) apply_lin<R, false>(psi, (R)a.b, (R)a.c, s, a.Ls, m);
-    R h[12], uh[12], U[18];
-    project<R>(mu, sg, psi, h);
-    load_link(lk + dir * 9, U);
-    su3_mul<R>(U, h, uh);
-    reconstruct_add<R>(mu, sg, uh, acc);
-  }
+  // Dh: forward (1 - g), backward (1 + g); Dh^dag flips both.
+  constexpr int SF = DAG ? -1 : 1;
+  hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
 
   double nrm2 = 0.0;
   if (PASS == PASS_A) {

@@ -33,7 +33,7 @@ enum {
 };
 // device scalar slots (doubles)
 enum {
-  D_PW = 0, D_RR = 1, D_RY = 2, D_RYN = 3 /* 2 */, D_BB = 6, D_TMP = 7,
+  D_PW = 0, D_RR = 1, D_RY = 2, D_RYN = 3 /* 2 */, D_BB = 6, D_TMP = 7, D_NREAL = 8,
   D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27
 };
 
@@ -116,52 +116,83 @@ static void apply_Q(Ctx& c, int sp, const uint4* t, uint4* out, const uint4* add
   char* q0 = A.qvec.as<char>();
   void* cin = q0;
   void* cout = q0 + nc * 16;
-  restrict_field(c, s, t, sp, cin, cp);
-  const int it = coarse_cg(c, A, cin, cout, prm.coarse_tol, prm.coarse_maxiter);
+  {
+    PhaseTimer pt(c, PH_TRANSFER);
+    restrict_field(c, s, t, sp, cin, cp);
+  }
+  int it = 0;
+  {
+    PhaseTimer pt(c, PH_COARSE);
+    it = coarse_cg(c, A, cin, cout, prm.coarse_tol, prm.coarse_maxiter);
+  }
   if (st) {
     st->coarse_iterations += it;
     if (it > st->coarse_iterations_max) st->coarse_iterations_max = it;
   }
+  PhaseTimer pt(c, PH_TRANSFER);
   prolong_field(c, s, cout, cp, out, sp, add);
 }
 
-// y = M1 r in precision op (A-DEF2) ; r in op
+// y = M1 r in precision op (A-DEF2) ; r in op.  M1 is linear (M_IRS runs a
+// fixed number of CG steps from zero; Q is linear), so a 16-bit preconditioner
+// runs on r scaled to unit RMS per real (keeping residual entries inside the
+// normal FP16 range) and its result is scaled back.
 static void apply_M1(Ctx& c, int op, int sp, const uint4* r, uint4* y, const hdcg_params& prm, hdcg_stats* st) {
   const uint4* rs = r;
-  if (sp != op) {
+  const bool scaled = is_16bit(sp);
+  if (scaled) {
+    norm2(c, r, op, 0, dsc(c, D_TMP));
+    uint4* t = c.scratch(sp, SL_RS);
+    convert_scaled(c, r, op, t, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0);
+    rs = t;
+  } else if (sp != op) {
     uint4* t = c.scratch(sp, SL_RS);
     convert_field(c, r, op, t, sp);
     rs = t;
   }
   uint4* z = c.scratch(sp, SL_Z);
-  int nm = 0;
-  cg_shifted(c, sp, rs, z, prm.mirs_shift, prm.mirs_iter, 0.0, prm.mirs_iter, &nm);
   uint4* t = c.scratch(sp, SL_T);
-  apply_mdagm(c, sp, z, t, nullptr, -1.0, 1.0, rs);  // t = r - H z
-  ++nm;
+  int nm = 0;
+  {
+    PhaseTimer pt(c, PH_H_SLOPPY);
+    cg_shifted(c, sp, rs, z, prm.mirs_shift, prm.mirs_iter, 0.0, prm.mirs_iter, &nm);
+    apply_mdagm(c, sp, z, t, nullptr, -1.0, 1.0, rs);  // t = r - H z
+    ++nm;
+  }
   if (st) st->n_mdagm_sloppy += nm;
   if (sp == op) {
     apply_Q(c, sp, t, y, z, prm, st);
   } else {
     uint4* ys = c.scratch(sp, SL_MRES);
     apply_Q(c, sp, t, ys, z, prm, st);
-    convert_field(c, ys, sp, y, op);
+    if (scaled) convert_scaled(c, ys, sp, y, op, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
+    else convert_field(c, ys, sp, y, op);
   }
 }
 
-// x_hi (FP64) = Q b
+// x_hi (FP64) = Q b  (16-bit: on b scaled to unit RMS, scaled back)
 static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdcg_params& prm, hdcg_stats* st) {
   uint4* bs = c.scratch(sp, SL_RS);
-  convert_field(c, b64, HDCG_F64, bs, sp);
+  const bool scaled = is_16bit(sp);
+  if (scaled) {
+    norm2(c, b64, HDCG_F64, 0, dsc(c, D_TMP));
+    convert_scaled(c, b64, HDCG_F64, bs, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0);
+  } else {
+    convert_field(c, b64, HDCG_F64, bs, sp);
+  }
   uint4* x0 = c.scratch(sp, SL_T);
   apply_Q(c, sp, bs, x0, nullptr, prm, st);
-  convert_field(c, x0, sp, xhi, HDCG_F64);
+  if (scaled) convert_scaled(c, x0, sp, xhi, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
+  else convert_field(c, x0, sp, xhi, HDCG_F64);
 }
 
 // r64 = b - H64 x_hi; returns |r64|^2 (host), r (op) = r64
 static double true_residual(Ctx& c, int op, const uint4* b64, const uint4* xhi, uint4* r, hdcg_stats* st) {
   uint4* r64 = c.scratch(HDCG_F64, SL_R64);
-  apply_mdagm(c, HDCG_F64, xhi, r64, nullptr, -1.0, 1.0, b64);
+  {
+    PhaseTimer pt(c, PH_H_F64);
+    apply_mdagm(c, HDCG_F64, xhi, r64, nullptr, -1.0, 1.0, b64);
+  }
   if (st) ++st->n_mdagm_f64;
   norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR));
   if (op != HDCG_F64) convert_field(c, r64, HDCG_F64, r, op);
@@ -188,6 +219,11 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
   uint4* yn = c.scratch(op, SL_YN);
   uint4* xhi = x64;
 
+  {
+    const double nreal = (double)c.n5 * 24.0;
+    HDCG_CUDA(cudaMemcpyAsync(dsc(c, D_NREAL), &nreal, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  }
   norm2(c, b64, HDCG_F64, 0, dsc(c, D_BB));
   double bb = 0.0;
   read_scalars(c, D_BB, 1, &bb);
@@ -218,7 +254,10 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
   int it = 0;
   int status = HDCG_NOT_CONVERGED;
   while (it < prm.maxiter) {
-    apply_mdagm(c, op, p, w, dsc(c, D_PW));
+    {
+      PhaseTimer pt(c, PH_H_OUTER);
+      apply_mdagm(c, op, p, w, dsc(c, D_PW));
+    }
     ++st->n_mdagm_outer;
     ScalarRef al;
     al.num = dsc(c, D_RY);
@@ -286,7 +325,11 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
       HDCG_CUDA(cudaMemcpyAsync(c.canon_in.p, bk, canon, cudaMemcpyHostToDevice, c.stream));
       canon_to_internal(c, c.canon_in.p, HDCG_F64, b64, HDCG_F64);
     }
-    const int rc = solve_one(c, b64, x64, tol, prm, st);
+    int rc;
+    {
+      PhaseTimer pt(c, PH_TOTAL);
+      rc = solve_one(c, b64, x64, tol, prm, st);
+    }
     if (rc != HDCG_OK) worst = rc;
     if (on_device) {
       internal_to_canon(c, x64, HDCG_F64, xk, HDCG_F64);
