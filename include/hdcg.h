@@ -173,7 +173,7 @@ typedef struct {
 } hdcg_stats;
 
 /* Fill p with the defaults (A-DEF2, FP32 outer, FP32 sloppy, M_IRS(7, 1.0),
- * coarse tol 0.04, flexible, reliable delta 0.1). */
+ * coarse tol 0.04, flexible, reliable delta 0.01). */
 void hdcg_default_params(hdcg_params* p);
 
 /* Solve H x = b for nrhs right-hand sides to |b - H x| / |b| <= tol (true FP64

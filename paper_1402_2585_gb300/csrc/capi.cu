@@ -308,7 +308,7 @@ void hdcg_default_params(hdcg_params* p) {
   p->coarse_maxiter = 1000;
   p->flexible = 1;
   p->maxiter = 10000;
-  p->reliable_delta = 0.1;
+  p->reliable_delta = 0.01;
 }
 
 int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p, hdcg_stats* st,

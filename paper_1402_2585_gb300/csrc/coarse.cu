@@ -779,8 +779,15 @@ void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec) {
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
 
-// y[a][j] = sum_l sum_k A[a][l][k][j] x[a + l][k]; one CTA per coarse site,
-// threads split over (j, slice of l)
+// y[a][j] = sum_l sum_k A[a][l][k][j] x[a + l][k].  The 81 couplings of a coarse
+// site are split over CGROUPS CTAs; CTA (a, g) writes its partial sum to
+// y_part[g][a][j] (consumers add the CGROUPS partials).  Within a CTA each warp
+// takes one coupling block at a time, lanes run over j (coalesced reads of the
+// transposed block A[a][l][k][:]) and the k loop is unrolled so that several
+// loads are in flight per lane.
+constexpr int CGROUPS = 3;
+constexpr int CWARPS = 8;
+
 template <typename AT, typename R>
 __device__ __forceinline__ void ld_a(const AT* p, R& re, R& im);
 template <> __device__ __forceinline__ void ld_a<double2, double>(const double2* p, double& re, double& im) {
@@ -800,60 +807,118 @@ template <> __device__ __forceinline__ void ld_a<__half2, float>(const __half2* 
 }
 
 template <typename AT, typename R>
-__global__ void __launch_bounds__(256) k_coarse_apply(const AT* __restrict__ A, const int* __restrict__ cnbr,
-                                                      int n, const typename CV<R>::T* __restrict__ x,
-                                                      typename CV<R>::T* y, int do_red, Reduction red) {
-  __shared__ double sre[256], sim[256];
-  const size_t a = blockIdx.x;
-  const int parts = blockDim.x / n;
-  const int j = threadIdx.x % n, part = threadIdx.x / n;
-  R sr = 0, si = 0;
-  if (part < parts) {
-    for (int l = part; l < 81; l += parts) {
-      const int nb = __ldg(cnbr + a * 81 + l);
-      const AT* row = A + ((a * 81 + l) * n) * n + j;
-      const typename CV<R>::T* xv = x + (size_t)nb * n;
-      for (int k = 0; k < n; ++k) {
-        R ar, ai;
-        ld_a<AT, R>(row + (size_t)k * n, ar, ai);
-        const typename CV<R>::T xk = xv[k];
-        sr += ar * xk.x - ai * xk.y;
-        si += ar * xk.y + ai * xk.x;
+__device__ __forceinline__ void capply_body(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
+                                            const typename CV<R>::T* __restrict__ x, typename CV<R>::T* ypart,
+                                            size_t nc, double* dot_out) {
+  __shared__ double sre[CWARPS][64], sim[CWARPS][64];
+  const size_t a = blockIdx.x / CGROUPS;
+  const int g = blockIdx.x % CGROUPS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l0 = g * 27, l1 = l0 + 27;
+  R sr0 = 0, si0 = 0, sr1 = 0, si1 = 0;   // j = lane, j = lane + 32
+  const int j0 = lane, j1 = lane + 32;
+  for (int l = l0 + w; l < l1; l += CWARPS) {
+    const int nb = __ldg(cnbr + a * 81 + l);
+    const AT* blk = A + ((a * 81 + l) * n) * n;
+    const typename CV<R>::T* xv = x + (size_t)nb * n;
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+      R ar[4], ai[4], br[4], bi[4];
+      typename CV<R>::T xk[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xk[u] = xv[k + u];
+        ar[u] = ai[u] = br[u] = bi[u] = 0;
+        if (j0 < n) ld_a<AT, R>(blk + (size_t)(k + u) * n + j0, ar[u], ai[u]);
+        if (j1 < n) ld_a<AT, R>(blk + (size_t)(k + u) * n + j1, br[u], bi[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sr0 += ar[u] * xk[u].x - ai[u] * xk[u].y;
+        si0 += ar[u] * xk[u].y + ai[u] * xk[u].x;
+        sr1 += br[u] * xk[u].x - bi[u] * xk[u].y;
+        si1 += br[u] * xk[u].y + bi[u] * xk[u].x;
       }
     }
+    for (; k < n; ++k) {
+      const typename CV<R>::T xk = xv[k];
+      R ar = 0, ai = 0, br = 0, bi = 0;
+      if (j0 < n) ld_a<AT, R>(blk + (size_t)k * n + j0, ar, ai);
+      if (j1 < n) ld_a<AT, R>(blk + (size_t)k * n + j1, br, bi);
+      sr0 += ar * xk.x - ai * xk.y;
+      si0 += ar * xk.y + ai * xk.x;
+      sr1 += br * xk.x - bi * xk.y;
+      si1 += br * xk.y + bi * xk.x;
+    }
   }
-  sre[threadIdx.x] = (double)sr;
-  sim[threadIdx.x] = (double)si;
+  sre[w][j0] = (double)sr0;
+  sim[w][j0] = (double)si0;
+  sre[w][j1] = (double)sr1;
+  sim[w][j1] = (double)si1;
   __syncthreads();
-  double v[1] = {0.0};
+  double dv = 0.0;
   if (threadIdx.x < n) {
     double tr = 0, ti = 0;
-    for (int p = 0; p < parts; ++p) {
-      tr += sre[p * n + threadIdx.x];
-      ti += sim[p * n + threadIdx.x];
+#pragma unroll
+    for (int q = 0; q < CWARPS; ++q) {
+      tr += sre[q][threadIdx.x];
+      ti += sim[q][threadIdx.x];
     }
-    y[a * n + threadIdx.x] = {(R)tr, (R)ti};
+    ypart[g * nc + a * n + threadIdx.x] = {(R)tr, (R)ti};
     const typename CV<R>::T xa = x[a * n + threadIdx.x];
-    v[0] = (double)xa.x * tr + (double)xa.y * ti;   // Re conj(x) y
+    dv = (double)xa.x * tr + (double)xa.y * ti;   // Re conj(x) y (partial over this group)
   }
+  *dot_out = dv;
+}
+
+template <typename AT, typename R>
+__global__ void __launch_bounds__(256) k_coarse_apply(const AT* __restrict__ A, const int* __restrict__ cnbr,
+                                                      int n, const typename CV<R>::T* __restrict__ x,
+                                                      typename CV<R>::T* ypart, size_t nc, int do_red,
+                                                      Reduction red) {
+  double dv = 0.0;
+  capply_body<AT, R>(A, cnbr, n, x, ypart, nc, &dv);
+  double v[1] = {dv};
   if (do_red) grid_reduce<1>(v, red);
 }
 
-void coarse_apply(Ctx& c, const Coarse& A, const void* x, void* y, double* xAx) {
-  const unsigned g = (unsigned)A.Vc;
+// y = sum of the CGROUPS partials
+template <typename R>
+__global__ void k_sum_groups(const typename CV<R>::T* ypart, typename CV<R>::T* y, size_t nc) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  typename CV<R>::T v = ypart[t];
+#pragma unroll
+  for (int g = 1; g < CGROUPS; ++g) {
+    const typename CV<R>::T u = ypart[g * nc + t];
+    v.x += u.x;
+    v.y += u.y;
+  }
+  y[t] = v;
+}
+
+template <typename AT, typename R>
+static void coarse_apply_t(Ctx& c, const Coarse& A, const void* x, void* y, double* xAx) {
+  using V = typename CV<R>::T;
+  const size_t nc = A.Vc * A.nvec;
+  DevMem part;
+  part.ensure(CGROUPS * nc * sizeof(V));
+  const unsigned g = (unsigned)(A.Vc * CGROUPS);
   Reduction red{};
   if (xAx) red = make_reduction(c, g, 1, xAx, 0);
-  if (A.prec == HDCG_F64)
-    k_coarse_apply<double2, double><<<g, 256, 0, c.stream>>>(A.A.as<double2>(), A.cnbr.as<int>(), A.nvec,
-                                                            (const double2*)x, (double2*)y, xAx != nullptr, red);
-  else if (A.prec == HDCG_F32)
-    k_coarse_apply<float2, float><<<g, 256, 0, c.stream>>>(A.A.as<float2>(), A.cnbr.as<int>(), A.nvec,
-                                                          (const float2*)x, (float2*)y, xAx != nullptr, red);
-  else
-    k_coarse_apply<__half2, float><<<g, 256, 0, c.stream>>>(A.A.as<__half2>(), A.cnbr.as<int>(), A.nvec,
-                                                           (const float2*)x, (float2*)y, xAx != nullptr, red);
+  k_coarse_apply<AT, R><<<g, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, (const V*)x, part.as<V>(),
+                                                 nc, xAx != nullptr, red);
+  k_sum_groups<R><<<(unsigned)((nc + 255) / 256), 256, 0, c.stream>>>(part.as<V>(), (V*)y, nc);
   HDCG_CUDA(cudaGetLastError());
-  ++c.launches;
+  c.launches += 2;
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void coarse_apply(Ctx& c, const Coarse& A, const void* x, void* y, double* xAx) {
+  HDCG_REQUIRE(A.nvec <= 64, HDCG_ERR_ARG, "nvec <= 64");
+  if (A.prec == HDCG_F64) coarse_apply_t<double2, double>(c, A, x, y, xAx);
+  else if (A.prec == HDCG_F32) coarse_apply_t<float2, float>(c, A, x, y, xAx);
+  else coarse_apply_t<__half2, float>(c, A, x, y, xAx);
 }
 
 // ---------------------------------------------------------------------------
@@ -893,43 +958,12 @@ __global__ void k_ccg_start(CCtl* ctl, double tol, int maxiter) {
 
 template <typename AT, typename R>
 __global__ void __launch_bounds__(256) k_ccg_apply(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
-                                                   const typename CV<R>::T* __restrict__ p, typename CV<R>::T* w,
-                                                   const CCtl* ctl, Reduction red) {
+                                                   const typename CV<R>::T* __restrict__ p, typename CV<R>::T* wpart,
+                                                   size_t nc, const CCtl* ctl, Reduction red) {
   if (ctl->done) return;
-  // same body as k_coarse_apply with the reduction always on
-  __shared__ double sre[256], sim[256];
-  const size_t a = blockIdx.x;
-  const int parts = blockDim.x / n;
-  const int j = threadIdx.x % n, part = threadIdx.x / n;
-  R sr = 0, si = 0;
-  if (part < parts) {
-    for (int l = part; l < 81; l += parts) {
-      const int nb = __ldg(cnbr + a * 81 + l);
-      const AT* row = A + ((a * 81 + l) * n) * n + j;
-      const typename CV<R>::T* xv = p + (size_t)nb * n;
-      for (int k = 0; k < n; ++k) {
-        R ar, ai;
-        ld_a<AT, R>(row + (size_t)k * n, ar, ai);
-        const typename CV<R>::T xk = xv[k];
-        sr += ar * xk.x - ai * xk.y;
-        si += ar * xk.y + ai * xk.x;
-      }
-    }
-  }
-  sre[threadIdx.x] = (double)sr;
-  sim[threadIdx.x] = (double)si;
-  __syncthreads();
-  double v[1] = {0.0};
-  if (threadIdx.x < n) {
-    double tr = 0, ti = 0;
-    for (int q = 0; q < parts; ++q) {
-      tr += sre[q * n + threadIdx.x];
-      ti += sim[q * n + threadIdx.x];
-    }
-    w[a * n + threadIdx.x] = {(R)tr, (R)ti};
-    const typename CV<R>::T pa = p[a * n + threadIdx.x];
-    v[0] = (double)pa.x * tr + (double)pa.y * ti;
-  }
+  double dv = 0.0;
+  capply_body<AT, R>(A, cnbr, n, p, wpart, nc, &dv);
+  double v[1] = {dv};
   grid_reduce<1>(v, red);
 }
 
@@ -943,7 +977,13 @@ __global__ void k_ccg_update(typename CV<R>::T* x, typename CV<R>::T* r, const t
   double v[1] = {0.0};
   if (t < nc) {
     typename CV<R>::T xv = x[t], rv = r[t];
-    const typename CV<R>::T pv = p[t], wv = w[t];
+    const typename CV<R>::T pv = p[t];
+    typename CV<R>::T wv = w[t];
+#pragma unroll
+    for (int g = 1; g < CGROUPS; ++g) {
+      wv.x += w[g * nc + t].x;
+      wv.y += w[g * nc + t].y;
+    }
     xv.x += al * pv.x;
     xv.y += al * pv.y;
     rv.x -= al * wv.x;
@@ -980,11 +1020,11 @@ template <typename AT, typename R>
 static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter) {
   using V = typename CV<R>::T;
   const size_t nc = A.Vc * A.nvec;
-  A.work.ensure(3 * nc * sizeof(V));
+  A.work.ensure((2 + CGROUPS) * nc * sizeof(V));
   A.ctl.ensure(sizeof(CCtl));
   V* r = A.work.as<V>();
   V* p = r + nc;
-  V* w = p + nc;
+  V* w = p + nc;   // CGROUPS partial products
   CCtl* ctl = A.ctl.as<CCtl>();
   const unsigned gv = (unsigned)((nc + 255) / 256);
   k_ccg_init<R><<<gv, 256, 0, c.stream>>>((const V*)rhs, (V*)sol, r, p, nc, make_reduction(c, gv, 1, &ctl->rr[0], 0));
@@ -996,8 +1036,9 @@ static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol
   while (true) {
     for (int b = 0; b < batch && queued < maxiter; ++b, ++queued) {
       const int par = queued & 1;
-      k_ccg_apply<AT, R><<<(unsigned)A.Vc, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, p, w, ctl,
-                                                               make_reduction(c, (unsigned)A.Vc, 1, &ctl->pAp, 0));
+      k_ccg_apply<AT, R><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(
+          A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, p, w, nc, ctl,
+          make_reduction(c, (unsigned)(A.Vc * CGROUPS), 1, &ctl->pAp, 0));
       k_ccg_update<R><<<gv, 256, 0, c.stream>>>((V*)sol, r, p, w, nc, ctl, par,
                                                 make_reduction(c, gv, 1, &ctl->rr[par ^ 1], 0));
       k_ccg_p<R><<<gv, 256, 0, c.stream>>>(p, r, nc, ctl, par, maxiter);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -109,7 +110,9 @@ struct Ctx {
 
   DevMem nbr[2];          // int32 [n4][8]: neighbour cb index of output site x (parity p)
   DevMem links[4][2];     // per link slot (F64, F32, F16, BF16) and output parity
-  DevMem scratch_f[5][20]; // work fields per precision (slot roles: solver.cu)
+  DevMem scratch_f[5][24]; // work fields per precision (slot roles: solver.cu; 20-23: hop autotuner)
+  std::map<int, int> hop_tuned;  // (prec, pass, fused, reduction) -> chosen hop variant
+  bool tuning_off = false;
   DevMem red_partials, red_ticket, scalars;
   DevMem canon_in, canon_out;  // canonical <-> internal staging
 
@@ -137,6 +140,14 @@ struct HopEpi {
   double sD = 1.0;
   double lam = 0.0;
   const uint4* extra = nullptr;
+  // fused CG step (see apply_mdagm_cg)
+  uint4* cg_x = nullptr;
+  uint4* cg_r = nullptr;
+  const uint4* cg_p = nullptr;
+  const double* al_num = nullptr;
+  const double* al_den0 = nullptr;
+  const double* al_den1 = nullptr;
+  double al_lam = 0.0;
 };
 
 void dwf_setup_tables(Ctx& c);
@@ -150,6 +161,12 @@ void apply_mpc(Ctx& c, int prec, const uint4* in, uint4* out, int dagger, double
 // out = sD * H in + lam * extra; mpc_norm2 (device double, may be null) gets |Mpc in|^2
 void apply_mdagm(Ctx& c, int prec, const uint4* in, uint4* out, double* mpc_norm2,
                  double sD = 1.0, double lam = 0.0, const uint4* extra = nullptr);
+
+// One CG step fused into H: w = H p + shift p (never stored);
+// alpha = *al_num / (*pw + shift * *pp); r -= alpha w; x += alpha p;
+// *pw <- |Mpc p|^2 (pass B), *rr_out <- |r|^2 (pass D).
+void apply_mdagm_cg(Ctx& c, int prec, const uint4* p, double shift, uint4* x, uint4* r, const double* al_num,
+                    const double* pw, const double* pp, double* rr_out);
 
 // ---------------------------------------------------------------------------
 // fields and BLAS-1 (blas.cu); all reductions accumulate in FP64

@@ -1,0 +1,388 @@
+// Device code of the fine-operator hop passes (see dwf.cu for the operator).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "context.h"
+
+namespace hdcg {
+
+struct HopArgs {
+  const uint4* in;
+  const uint4* in2;
+  const uint4* extra;
+  uint4* out;
+  const void* links;
+  const int* nbr;
+  size_t n5;
+  int Ls, lslog2;
+  double b, c, alpha, beta, mass, minv_norm, rpow[6];
+  double sD, lam;
+  Reduction red;
+  int do_red;
+  // fused CG step in pass D (cg_r != null): w = out is not stored; instead
+  // alpha = *al_num / (*al_den0 + al_lam * *al_den1), r -= alpha w, x += alpha p,
+  // and the reduction receives |r|^2
+  uint4* cg_x;
+  uint4* cg_r;
+  const uint4* cg_p;
+  const double* al_num;
+  const double* al_den0;
+  const double* al_den1;
+  double al_lam;
+};
+
+// ------------------------------------------------------------------------------
+// link loads: 9 complex of one link into 18 reals.  Links are stored padded to
+// whole 16-byte granules (LINK_GRAN[prec] granules per link) so that one link
+// is read with 16-byte loads: FP64 9, FP32 5, 16-bit 3 granules.
+// ------------------------------------------------------------------------------
+template <typename LT> struct LinkGran;
+template <> struct LinkGran<double2> { static constexpr int g = 9; };
+template <> struct LinkGran<float2> { static constexpr int g = 5; };
+template <> struct LinkGran<__half2> { static constexpr int g = 3; };
+template <> struct LinkGran<__nv_bfloat162> { static constexpr int g = 3; };
+
+__device__ __forceinline__ void load_link(const double2*, const uint4* __restrict__ p, double* u) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const uint4 g = __ldg(p + i);
+    u[2 * i] = __hiloint2double(g.y, g.x);
+    u[2 * i + 1] = __hiloint2double(g.w, g.z);
+  }
+}
+__device__ __forceinline__ void load_link(const float2*, const uint4* __restrict__ p, float* u) {
+  // 8-byte loads keep the register footprint of the FP32 kernels low
+  const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float2 v = __ldg(q + i);
+    u[2 * i] = v.x;
+    u[2 * i + 1] = v.y;
+  }
+}
+template <typename H2>
+__device__ __forceinline__ void load_link16(const uint4* __restrict__ p, float* u, bool bf) {
+  unsigned t[12];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const uint4 g = __ldg(p + i);
+    t[4 * i] = g.x;
+    t[4 * i + 1] = g.y;
+    t[4 * i + 2] = g.z;
+    t[4 * i + 3] = g.w;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float2 v = bf ? b2f(t[i]) : h2f(t[i]);
+    u[2 * i] = v.x;
+    u[2 * i + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void load_link(const __half2*, const uint4* __restrict__ p, float* u) {
+  load_link16<__half2>(p, u, false);
+}
+__device__ __forceinline__ void load_link(const __nv_bfloat162*, const uint4* __restrict__ p, float* u) {
+  load_link16<__nv_bfloat162>(p, u, true);
+}
+
+// ------------------------------------------------------------------------------
+// s-direction operators on one lane's 24 reals; spins 0,1 are chirality +
+// (gamma5 = +1), spins 2,3 chirality -.  P_s acts on chirality + as the down
+// shift (psi_{s-1}) and on chirality - as the up shift (psi_{s+1}); P_s^dag
+// swaps them.  Wrapped values pick up -m.
+// ------------------------------------------------------------------------------
+template <typename R, bool DAG>
+__device__ __forceinline__ void apply_Ppow(R* v, int d, int s, int Ls, R m) {
+  const int up_src = (s + d) & (Ls - 1);
+  const R up_f = (s + d >= Ls) ? -m : R(1);
+  const int dn_src = (s - d) & (Ls - 1);
+  const R dn_f = (s < d) ? -m : R(1);
+  const int sp = DAG ? up_src : dn_src;
+  const R fp = DAG ? up_f : dn_f;
+  const int sm = DAG ? dn_src : up_src;
+  const R fm = DAG ? dn_f : up_f;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) v[i] = fp * __shfl_sync(FULL_MASK, v[i], sp, Ls);
+#pragma unroll
+  for (int i = 12; i < 24; ++i) v[i] = fm * __shfl_sync(FULL_MASK, v[i], sm, Ls);
+}
+
+// v <- a v + b P v
+template <typename R, bool DAG>
+__device__ __forceinline__ void apply_lin(R* v, R a, R b, int s, int Ls, R m) {
+  R t[24];
+#pragma unroll
+  for (int i = 0; i < 24; ++i) t[i] = v[i];
+  apply_Ppow<R, DAG>(t, 1, s, Ls, m);
+#pragma unroll
+  for (int i = 0; i < 24; ++i) v[i] = a * v[i] + b * t[i];
+}
+
+// v <- M_ee^-1 v (DAG: M_ee^-dag) by doubling: A_{j+1} = A_j + r^{2^j} P^{2^j} A_j
+template <typename R, bool DAG>
+__device__ __forceinline__ void apply_minv(R* v, int s, const HopArgs& a) {
+  const R m = (R)a.mass;
+  for (int j = 0; j < a.lslog2; ++j) {
+    R t[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) t[i] = v[i];
+    apply_Ppow<R, DAG>(t, 1 << j, s, a.Ls, m);
+    const R rp = (R)a.rpow[j];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) v[i] += rp * t[i];
+  }
+  const R nrm = (R)a.minv_norm;
+#pragma unroll
+  for (int i = 0; i < 24; ++i) v[i] *= nrm;
+}
+
+// ------------------------------------------------------------------------------
+// spin projection (1 - SG gamma_MU) in the chiral basis:
+//   h = u - SG A_mu l,  result = (h, -SG B_mu h),  with A_mu, B_mu the 2x2
+//   off-diagonal blocks of gamma_mu (A_mu B_mu = 1):
+//   A_x l = (-i l1, -i l0), A_y l = (-l1, l0), A_z l = (-i l0, i l1), A_t l = (l0, l1)
+//   B_x h = (i h1, i h0),   B_y h = (h1, -h0), B_z h = (i h0, -i h1), B_t h = (h0, h1)
+// spinor reals index: (spin * 3 + colour) * 2 + {re, im}
+// ------------------------------------------------------------------------------
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void project(const R* p, R* h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R u0r = p[(0 * 3 + c) * 2], u0i = p[(0 * 3 + c) * 2 + 1];
+    const R u1r = p[(1 * 3 + c) * 2], u1i = p[(1 * 3 + c) * 2 + 1];
+    const R l0r = p[(2 * 3 + c) * 2], l0i = p[(2 * 3 + c) * 2 + 1];
+    const R l1r = p[(3 * 3 + c) * 2], l1i = p[(3 * 3 + c) * 2 + 1];
+    R a0r, a0i, a1r, a1i;  // A_mu l
+    if (MU == 0) { a0r = l1i; a0i = -l1r; a1r = l0i; a1i = -l0r; }
+    else if (MU == 1) { a0r = -l1r; a0i = -l1i; a1r = l0r; a1i = l0i; }
+    else if (MU == 2) { a0r = l0i; a0i = -l0r; a1r = -l1i; a1i = l1r; }
+    else { a0r = l0r; a0i = l0i; a1r = l1r; a1i = l1i; }
+    if (SG > 0) {
+      h[(0 * 3 + c) * 2] = u0r - a0r; h[(0 * 3 + c) * 2 + 1] = u0i - a0i;
+      h[(1 * 3 + c) * 2] = u1r - a1r; h[(1 * 3 + c) * 2 + 1] = u1i - a1i;
+    } else {
+      h[(0 * 3 + c) * 2] = u0r + a0r; h[(0 * 3 + c) * 2 + 1] = u0i + a0i;
+      h[(1 * 3 + c) * 2] = u1r + a1r; h[(1 * 3 + c) * 2 + 1] = u1i + a1i;
+    }
+  }
+}
+
+// acc += (uh, -SG B_mu uh)
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void reconstruct_add(const R* uh, R* acc) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R h0r = uh[(0 * 3 + c) * 2], h0i = uh[(0 * 3 + c) * 2 + 1];
+    const R h1r = uh[(1 * 3 + c) * 2], h1i = uh[(1 * 3 + c) * 2 + 1];
+    R b0r, b0i, b1r, b1i;  // B_mu h
+    if (MU == 0) { b0r = -h1i; b0i = h1r; b1r = -h0i; b1i = h0r; }
+    else if (MU == 1) { b0r = h1r; b0i = h1i; b1r = -h0r; b1i = -h0i; }
+    else if (MU == 2) { b0r = -h0i; b0i = h0r; b1r = h1i; b1i = -h1r; }
+    else { b0r = h0r; b0i = h0i; b1r = h1r; b1i = h1i; }
+    acc[(0 * 3 + c) * 2] += h0r;
+    acc[(0 * 3 + c) * 2 + 1] += h0i;
+    acc[(1 * 3 + c) * 2] += h1r;
+    acc[(1 * 3 + c) * 2 + 1] += h1i;
+    if (SG > 0) {
+      acc[(2 * 3 + c) * 2] -= b0r; acc[(2 * 3 + c) * 2 + 1] -= b0i;
+      acc[(3 * 3 + c) * 2] -= b1r; acc[(3 * 3 + c) * 2 + 1] -= b1i;
+    } else {
+      acc[(2 * 3 + c) * 2] += b0r; acc[(2 * 3 + c) * 2 + 1] += b0i;
+      acc[(3 * 3 + c) * 2] += b1r; acc[(3 * 3 + c) * 2 + 1] += b1i;
+    }
+  }
+}
+
+// uh[sp][a] = sum_b U[a][b] h[sp][b]
+template <typename R>
+__device__ __forceinline__ void su3_mul(const R* U, const R* h, R* uh) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R re = 0, im = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R ur = U[(a * 3 + b) * 2], ui = U[(a * 3 + b) * 2 + 1];
+        const R hr = h[(sp * 3 + b) * 2], hi = h[(sp * 3 + b) * 2 + 1];
+        re += ur * hr - ui * hi;
+        im += ur * hi + ui * hr;
+      }
+      uh[(sp * 3 + a) * 2] = re;
+      uh[(sp * 3 + a) * 2 + 1] = im;
+    }
+}
+
+template <typename St> struct LinkOf;
+template <> struct LinkOf<f64_t> { using T = double2; };
+template <> struct LinkOf<f32_t> { using T = float2; };
+template <> struct LinkOf<f16_t> { using T = __half2; };
+template <> struct LinkOf<bf16_t> { using T = __nv_bfloat162; };
+template <> struct LinkOf<bf16t_t> { using T = __nv_bfloat162; };
+
+// both hops along direction MU: forward (x + mu, projector 1 - SF g) and
+// backward (x - mu, projector 1 + SF g); the two neighbour spinors and links are
+// loaded before either is used so that their loads overlap.
+template <typename St, typename R, typename LT, int MU, int SF, bool KIN>
+__device__ __forceinline__ void hop_pair(const HopArgs& a, const int* nbv, const uint4* lk, int s, R* acc) {
+  constexpr int LG = LinkGran<LT>::g;
+  R pf[24], pb[24];
+  load_spinor<St, R>(a.in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
+  load_spinor<St, R>(a.in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
+  if (KIN) {
+    const R m = (R)a.mass;
+    apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
+    apply_lin<R, false>(pb, (R)a.b, (R)a.c, s, a.Ls, m);
+  }
+  R h[12], uh[12], U[18];
+  project<MU, SF>(pf, h);
+  load_link((const LT*)nullptr, lk + MU * LG, U);
+  su3_mul<R>(U, h, uh);
+  reconstruct_add<MU, SF>(uh, acc);
+  project<MU, -SF>(pb, h);
+  load_link((const LT*)nullptr, lk + (MU + 4) * LG, U);
+  su3_mul<R>(U, h, uh);
+  reconstruct_add<MU, -SF>(uh, acc);
+}
+
+// ------------------------------------------------------------------------------
+// one hop pass
+// ------------------------------------------------------------------------------
+// MINB: minimum resident CTAs per SM requested from the compiler (register
+// budget); the variants are chosen at run time by the hop autotuner.
+template <typename St, int PASS, bool MOB, int MINB>
+__global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
+  using R = typename Store<St>::real;
+  using LT = typename LinkOf<St>::T;
+  constexpr bool DAG = (PASS == PASS_C || PASS == PASS_D);
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = gtid < a.n5;
+  const int s = threadIdx.x & (a.Ls - 1);
+  const size_t x4 = active ? (gtid >> a.lslog2) : 0;
+  const size_t site5 = x4 * a.Ls + s;
+  const R m = (R)a.mass;
+
+  R acc[24];
+#pragma unroll
+  for (int i = 0; i < 24; ++i) acc[i] = 0;
+
+  // all eight neighbour indices at once (32 bytes, shared by the Ls lanes of a site)
+  const int4 nb0 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2);
+  const int4 nb1 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2 + 1);
+  const int nbv[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
+  const uint4* lk = reinterpret_cast<const uint4*>(a.links) + x4 * 8 * LinkGran<LT>::g;
+  // Dh: forward (1 - g), backward (1 + g); Dh^dag flips both.
+  constexpr int SF = DAG ? -1 : 1;
+  hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+
+  double nrm2 = 0.0;
+  if (PASS == PASS_A) {
+    apply_minv<R, false>(acc, s, a);
+    if (MOB) {
+      apply_lin<R, false>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+    } else {
+      const R bb = (R)(a.b * a.b);
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] *= bb;
+    }
+  } else if (PASS == PASS_C) {
+    if (MOB) {
+      apply_lin<R, true>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] *= (R)a.b;
+    }
+    apply_minv<R, true>(acc, s, a);
+  } else {
+    // B, D: out = M_oo^(dag) in2 - K^(dag) acc / 4   (B has no K on this side)
+    if (PASS == PASS_D) {
+      if (MOB) {
+        apply_lin<R, true>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] *= (R)a.b;
+      }
+    }
+    R self[24];
+    load_spinor<St, R>(a.in2, site5, a.n5, self);
+    apply_lin<R, DAG>(self, (R)a.alpha, (R)a.beta, s, a.Ls, m);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) acc[i] = self[i] - R(0.25) * acc[i];
+    if (PASS == PASS_D) {
+      const R sD = (R)a.sD;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] *= sD;
+      if (a.extra) {
+        R ex[24];
+        load_spinor<St, R>(a.extra, site5, a.n5, ex);
+        const R lam = (R)a.lam;
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] += lam * ex[i];
+      }
+    }
+  }
+  if (PASS == PASS_D && a.cg_r) {
+    double den = *a.al_den0;
+    if (a.al_den1) den += a.al_lam * (*a.al_den1);
+    const R alpha = (R)(den != 0.0 ? *a.al_num / den : 0.0);
+    if (active) {
+      R rv[24], xv[24], pv[24];
+      load_spinor<St, R>(a.cg_r, site5, a.n5, rv);
+      load_spinor<St, R>(a.cg_x, site5, a.n5, xv);
+      load_spinor<St, R>(a.cg_p, site5, a.n5, pv);
+#pragma unroll
+      for (int i = 0; i < 24; ++i) {
+        rv[i] -= alpha * acc[i];
+        xv[i] += alpha * pv[i];
+        acc[i] = rv[i];
+      }
+      store_spinor<St, R>(a.cg_r, site5, a.n5, rv);
+      store_spinor<St, R>(a.cg_x, site5, a.n5, xv);
+    }
+  } else if (active) {
+    store_spinor<St, R>(a.out, site5, a.n5, acc);
+  }
+  if (a.do_red) {
+    if (active) {
+      R t = 0;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) t += acc[i] * acc[i];
+      nrm2 = (double)t;
+    }
+    double v[1] = {nrm2};
+    grid_reduce<1>(v, a.red);
+  }
+}
+
+
+constexpr int HOP_VARIANTS = 3;  // MINB = 1, 2, 3
+
+// launch variant v (0..2) of one pass for storage St
+template <typename St>
+void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st) {
+#define HDCG_HOP_CASE(P, M)                                                      \
+  if (pass == P && v == M - 1) {                                                 \
+    if (mob) hop_kernel<St, P, true, M><<<grid, 256, 0, st>>>(a);               \
+    else hop_kernel<St, P, false, M><<<grid, 256, 0, st>>>(a);                  \
+    return;                                                                      \
+  }
+  HDCG_HOP_CASE(PASS_A, 1) HDCG_HOP_CASE(PASS_A, 2) HDCG_HOP_CASE(PASS_A, 3)
+  HDCG_HOP_CASE(PASS_B, 1) HDCG_HOP_CASE(PASS_B, 2) HDCG_HOP_CASE(PASS_B, 3)
+  HDCG_HOP_CASE(PASS_C, 1) HDCG_HOP_CASE(PASS_C, 2) HDCG_HOP_CASE(PASS_C, 3)
+  HDCG_HOP_CASE(PASS_D, 1) HDCG_HOP_CASE(PASS_D, 2) HDCG_HOP_CASE(PASS_D, 3)
+#undef HDCG_HOP_CASE
+}
+
+// explicit instantiations live in dwf_<prec>.cu
+void launch_hop_f64(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+void launch_hop_f32(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+void launch_hop_f16(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+void launch_hop_bf16(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+void launch_hop_bf16t(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+
+}  // namespace hdcg

@@ -61,7 +61,6 @@ static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, 
                       int maxiter, int* n_mdagm) {
   uint4* res = c.scratch(prec, SL_MRES);
   uint4* p = c.scratch(prec, SL_MP);
-  uint4* w = c.scratch(prec, SL_MW);
   zero_field(c, x, prec);
   copy_field(c, prec, b, res);
   copy_field(c, prec, b, p);
@@ -76,14 +75,9 @@ static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, 
   int it = 0;
   for (; it < nit; ++it) {
     const int par = it & 1;
-    apply_mdagm(c, prec, p, w, dsc(c, D_MPW), 1.0, shift, shift != 0.0 ? p : nullptr);
+    apply_mdagm_cg(c, prec, p, shift, x, res, dsc(c, D_MRR + par), dsc(c, D_MPW), dsc(c, D_MPP),
+                   dsc(c, D_MRR + (par ^ 1)));
     if (n_mdagm) ++*n_mdagm;
-    ScalarRef al;
-    al.num = dsc(c, D_MRR + par);
-    al.den0 = dsc(c, D_MPW);
-    al.den1 = dsc(c, D_MPP);
-    al.lam = shift;
-    update_xr(c, prec, x, prec, p, res, w, al, 1, dsc(c, D_MRR + (par ^ 1)));
     if (niter_fixed <= 0) {
       double rr = 0.0;
       read_scalars(c, D_MRR + (par ^ 1), 1, &rr);
@@ -214,7 +208,6 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
   uint4* xlo = c.scratch(op, SL_XLO);
   uint4* r = c.scratch(op, SL_R);
   uint4* p = c.scratch(op, SL_P);
-  uint4* w = c.scratch(op, SL_W);
   uint4* y = c.scratch(op, SL_Y);
   uint4* yn = c.scratch(op, SL_YN);
   uint4* xhi = x64;
@@ -256,13 +249,9 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
   while (it < prm.maxiter) {
     {
       PhaseTimer pt(c, PH_H_OUTER);
-      apply_mdagm(c, op, p, w, dsc(c, D_PW));
+      apply_mdagm_cg(c, op, p, 0.0, xlo, r, dsc(c, D_RY), dsc(c, D_PW), nullptr, dsc(c, D_RR));
     }
     ++st->n_mdagm_outer;
-    ScalarRef al;
-    al.num = dsc(c, D_RY);
-    al.den0 = dsc(c, D_PW);
-    update_xr(c, op, xlo, op, p, r, w, al, 1, dsc(c, D_RR));
     ++it;
     double h[2];
     read_scalars(c, D_PW, 2, h);  // pw, rr
