@@ -333,6 +333,37 @@ def run_apply_only(args, w):
                       "ms_per_apply": e0.elapsed_time(e1) / args.apply_only}), flush=True)
 
 
+def run_coarse_only(args, w):
+    """A small case for kernel profiling: the workload's coarse operator
+    (subspace = block-orthonormalised Gaussian vectors, no inverse iteration)
+    applied ``args.coarse_only`` times through hdcg_coarse_apply."""
+    import torch
+
+    from paper_1402_2585_gb300 import Hdcg
+    prec = PREC[w.prec]
+    sub_prec = prec if prec in (0, 1) else 2
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
+    h.set_dwf(w.M5, w.b, w.c, w.mass)
+    h.set_gauge(torch.from_numpy(sy.gauge_field(w.dims, w.eps, w.gauge_seed)).to(dev))
+    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=0, seed=w.subspace_seed)
+    h.build_coarse(sub_prec if sub_prec != 2 else 2)
+    vc = 1
+    for d, b in zip(w.dims, w.block):
+        vc *= d // b
+    x = torch.view_as_real(torch.from_numpy(sy.coarse_gaussian(vc, w.nvec, 5))).to(dev).contiguous()
+    y = torch.empty_like(x)
+    h.coarse_apply(x, y)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.coarse_only):
+        h.coarse_apply(x, y)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"workload": w.name, "coarse_applies": args.coarse_only,
+                      "ms_per_call": (time.perf_counter() - t0) * 1e3 / args.coarse_only}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,9 +374,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling case: run this many H applies only (no solve)")
+    ap.add_argument("--coarse-only", type=int, default=0,
+                    help="profiling case: build the coarse operator and apply it this many times")
     args = ap.parse_args()
     w = sy.WORKLOADS[args.workload]
-    if args.apply_only:
+    if args.coarse_only:
+        run_coarse_only(args, w)
+    elif args.apply_only:
         run_apply_only(args, w)
     elif args.impl == "reference":
         run_reference(args, w)
