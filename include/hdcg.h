@@ -143,6 +143,24 @@ int hdcg_prolong(hdcg_t h, const void* c, void* v, int prec);
 /* y = A x on canonical coarse vectors (complex double, device). */
 int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
 
+/* y = A x exactly like hdcg_coarse_apply, but without allocating any device
+ * memory: for callers that cannot call cudaMalloc on this path (for example a
+ * host code that hands all device memory to its own pool allocator, or one
+ * that must not grow its footprint while other work is resident).  The paper
+ * has no counterpart; it is a property of this library's interface.
+ * Scratch (the coarse vectors in the working precision and three partial
+ * products) lives in a fixed 32 MiB device array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limit: 838,860 coarse unknowns (Vc * Nvec) with an FP32/FP16 coarse
+ * operator, 699,050 with FP64; larger operators are rejected with
+ * HDCG_ERR_ARG and a message giving the bytes needed.  The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  All calls on a device share
+ * the array: calls that overlap on the GPU (several streams or host threads)
+ * race.  x, y: canonical coarse vectors, complex double, device.
+ * Synchronous. */
+int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y);
+
 /* ---------------------------------------------------------------------------
  * Solve H x = b
  * ------------------------------------------------------------------------- */

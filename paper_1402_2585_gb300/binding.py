@@ -73,6 +73,7 @@ _SIGS = {
     "hdcg_restrict": (_I, [_P, _P, _I, _P]),
     "hdcg_prolong": (_I, [_P, _P, _P, _I]),
     "hdcg_coarse_apply": (_I, [_P, _P, _P]),
+    "hdcg_coarse_apply_noalloc": (_I, [_P, _P, _P]),
     "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
     "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
     "hdcg_set_profiling": (_I, [_P, _I]),
@@ -199,6 +200,9 @@ class Hdcg:
 
     def coarse_apply(self, x, y):
         return self._check(self._L.hdcg_coarse_apply(self.h, _ptr(x), _ptr(y)))
+
+    def coarse_apply_noalloc(self, x, y):
+        return self._check(self._L.hdcg_coarse_apply_noalloc(self.h, _ptr(x), _ptr(y)))
 
     # -- solve ----------------------------------------------------------------
     @staticmethod

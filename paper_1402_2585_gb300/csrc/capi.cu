@@ -296,6 +296,16 @@ int hdcg_coarse_apply(hdcg_t h, const void* x, void* y) {
   return HDCG_OK;
 }
 
+int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y) {
+  HDCG_ENTRY(h, {
+    check_ptr(x, "x");
+    check_ptr(y, "y");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    coarse_apply_noalloc(c, *c.coarse, x, y);
+  });
+  return HDCG_OK;
+}
+
 void hdcg_default_params(hdcg_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));

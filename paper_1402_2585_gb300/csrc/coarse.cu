@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -1109,6 +1110,90 @@ void coarse_export(Ctx& c, const Coarse& A, void* host) {
   ++c.launches;
   HDCG_CUDA(cudaMemcpyAsync(host, d.p, tot * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// ---------------------------------------------------------------------------
+// Coarse stencil apply that allocates nothing (hdcg_coarse_apply_noalloc).
+// Its scratch -- the coarse vectors in the working precision and the
+// CGROUPS partial products -- lives in one file-scope device array of fixed
+// size instead of memory obtained from cudaMalloc, for callers that must not
+// allocate device memory on this path.  Every GPU that loads the library
+// holds the array until the process exits.  All calls on a device share it
+// and it keeps the previous call's contents; nothing in it needs to start at
+// zero because every call overwrites all the bytes it reads.  Calls that
+// overlap on the GPU (other streams, other host threads) race on it.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256] = {};
+
+// Device address of the array on the current device: looked up once per
+// device with that device current (the first call on a device does this set-up).
+static char* noalloc_scratch() {
+  int dev = 0;
+  HDCG_CUDA(cudaGetDevice(&dev));
+  HDCG_REQUIRE(dev >= 0 && dev < 256, HDCG_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      throw Error{HDCG_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") + cudaGetErrorString(e)};
+    g_noalloc_addr[dev] = p;
+  }
+  return reinterpret_cast<char*>(g_noalloc_addr[dev]);
+}
+
+size_t coarse_apply_noalloc_bytes(const Coarse& A) {
+  const size_t nc = A.Vc * A.nvec;
+  // FP64 vectors: the caller's buffers are used directly, scratch = partials;
+  // FP32 vectors: converted x, y and the partials
+  return A.vec_prec() == HDCG_F64 ? CGROUPS * nc * sizeof(double2) : (2 + CGROUPS) * nc * sizeof(float2);
+}
+
+template <typename AT, typename R>
+static void coarse_apply_noalloc_t(Ctx& c, const Coarse& A, const void* x64, void* y64) {
+  using V = typename CV<R>::T;
+  const size_t nc = A.Vc * A.nvec;
+  char* arena = noalloc_scratch();
+  const unsigned gv = (unsigned)((nc + 255) / 256);
+  const V* x;
+  V* y;
+  V* part;
+  if (sizeof(V) == sizeof(double2)) {
+    x = reinterpret_cast<const V*>(x64);
+    y = reinterpret_cast<V*>(y64);
+    part = reinterpret_cast<V*>(arena);
+  } else {
+    V* xs = reinterpret_cast<V*>(arena);
+    V* ys = xs + nc;
+    part = ys + nc;
+    k_cvec_convert<double2, V><<<gv, 256, 0, c.stream>>>(reinterpret_cast<const double2*>(x64), xs, nc);
+    ++c.launches;
+    x = xs;
+    y = ys;
+  }
+  k_coarse_apply<AT, R><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, x,
+                                                                          part, nc, 0, Reduction{});
+  k_sum_groups<R><<<gv, 256, 0, c.stream>>>(part, y, nc);
+  c.launches += 2;
+  if (sizeof(V) != sizeof(double2)) {
+    k_cvec_convert<V, double2><<<gv, 256, 0, c.stream>>>(y, reinterpret_cast<double2*>(y64), nc);
+    ++c.launches;
+  }
+  HDCG_CUDA(cudaGetLastError());
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64) {
+  HDCG_REQUIRE(A.nvec <= 64, HDCG_ERR_ARG, "nvec <= 64");
+  const size_t need = coarse_apply_noalloc_bytes(A);
+  if (need > NOALLOC_SCRATCH_BYTES)
+    throw Error{HDCG_ERR_ARG, "coarse operator too large for the no-alloc scratch: needs " + std::to_string(need) +
+                                  " bytes, limit " + std::to_string((size_t)NOALLOC_SCRATCH_BYTES) + " bytes"};
+  if (A.prec == HDCG_F64) coarse_apply_noalloc_t<double2, double>(c, A, x64, y64);
+  else if (A.prec == HDCG_F32) coarse_apply_noalloc_t<float2, float>(c, A, x64, y64);
+  else coarse_apply_noalloc_t<__half2, float>(c, A, x64, y64);
 }
 
 }  // namespace hdcg

@@ -60,6 +60,12 @@ void coarse_apply(Ctx& c, const Coarse& A, const void* x, void* y, double* xAx);
 int coarse_cg(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter);
 // coarse vectors: complex double <-> coarse vector precision (n complex)
 void cvec_convert(Ctx& c, const void* in, int pin, void* out, int pout, size_t n);
+// Size of the fixed device array behind the no-alloc coarse apply (32 MiB:
+// up to 838,860 coarse unknowns with FP32/FP16 A, 699,050 with FP64 A).
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
+size_t coarse_apply_noalloc_bytes(const Coarse& A);
+// y = A x on canonical complex double coarse vectors (device) without allocating
+void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64);
 // canonical export of A (complex double [Vc][81][j][k], host)
 void coarse_export(Ctx& c, const Coarse& A, void* host);
 
