@@ -181,23 +181,31 @@ def run_ours(args, w):
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(U).to(dev))
     t_sub0 = time.perf_counter()
-    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=3, inv_shift=0.0, inv_tol=1e-4, inv_maxiter=20000,
-                     seed=w.subspace_seed + rank)
+    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=args.inv_steps, inv_shift=0.0, inv_tol=args.inv_tol,
+                     inv_maxiter=20000, seed=w.subspace_seed + rank)
     t_sub = time.perf_counter() - t_sub0
     t_c0 = time.perf_counter()
+    if args.coarse_prec:
+        coarse_prec = PREC[args.coarse_prec]
     h.build_coarse(coarse_prec)
     t_coarse = time.perf_counter() - t_c0
     setup_s = time.perf_counter() - t_setup0
 
     outer = 0 if prec == 0 else 1
-    prm = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000)
-    prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000)
-    b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, w.source_seed + rank)).to(dev)
+    nrhs = w.nrhs
+    prm = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000,
+                              reliable_delta=args.reliable_delta, batch=1)
+    prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000,
+                                 reliable_delta=args.reliable_delta)
+    if nrhs == 1:
+        b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, w.source_seed + rank)).to(dev)
+    else:
+        b = torch.from_numpy(sy.point_sources(w.dims, w.Ls, nrhs)).to(dev)
     x = torch.zeros_like(b)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
-        h.solve(b, x, w.tol, prm)
+        h.solve(b, x, w.tol, prm, nrhs=nrhs)
     barrier()
 
     clk = ClockSampler(local)
@@ -212,7 +220,7 @@ def run_ours(args, w):
         barrier()
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
-        st = h.solve(b, x, w.tol, prm)
+        st = h.solve(b, x, w.tol, prm, nrhs=nrhs)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         torch.cuda.nvtx.range_pop()
@@ -238,7 +246,7 @@ def run_ours(args, w):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        cg_stats = h.solve(b, x, w.tol, prm_cg).as_dict()
+        cg_stats = h.solve(b, x, w.tol, prm_cg, nrhs=nrhs).as_dict()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         cg_times.append(e0.elapsed_time(e1) / 1e3)
@@ -252,9 +260,24 @@ def run_ours(args, w):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        h.solve(bh, xh, w.tol, prm)
+        h.solve(bh, xh, w.tol, prm, nrhs=nrhs)
         e2e.append(time.perf_counter() - t0)
-    nbytes = bh.numel() * bh.element_size()
+    nbytes = bh.numel() * bh.element_size()  # all right-hand sides of one step
+
+    seq = None
+    if nrhs > 1:
+        prm_seq = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000,
+                                      reliable_delta=args.reliable_delta, batch=0)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sq = h.solve(b, x, w.tol, prm_seq, nrhs=nrhs).as_dict()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations_total": sq["iterations"],
+               "true_residual": sq["true_residual"]}
 
     if rank != 0:
         if world > 1:
@@ -276,7 +299,8 @@ def run_ours(args, w):
         "data": "synthetic",
         "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "M5": w.M5, "b": w.b, "c": w.c,
                    "mass": w.mass, "eps": w.eps, "block": list(w.block), "nvec": w.nvec, "tol": w.tol,
-                   "storage": w.prec, "rhs_per_gpu": 1, "l2": "flushed (512 MiB write) before each step",
+                   "storage": w.prec, "rhs_per_gpu": nrhs, "coarse_storage": args.coarse_prec or None,
+                   "l2": "flushed (512 MiB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
@@ -295,7 +319,10 @@ def run_ours(args, w):
                  "n_mdagm_f64": s0["n_mdagm_f64"], "reliable_updates": s0["reliable_updates"],
                  "true_residual": s0["true_residual"]},
         "phases_ms_per_solve": phases,
-        "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse},
+        "sequential_single_rhs": seq,
+        "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse,
+                          "inverse_iteration": {"steps": args.inv_steps, "tol": args.inv_tol}},
+        "reliable_delta": args.reliable_delta,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -372,6 +399,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sy.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inv-steps", type=int, default=3, help="inverse-iteration steps of the subspace setup")
+    ap.add_argument("--inv-tol", type=float, default=1e-4, help="CG tolerance of each inverse-iteration step")
+    ap.add_argument("--reliable-delta", type=float, default=0.01, help="FP64 true-residual update factor")
+    ap.add_argument("--coarse-prec", choices=["f64", "f32", "f16"], default=None,
+                    help="storage of the little Dirac operator (default: the workload's)")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling case: run this many H applies only (no solve)")
     ap.add_argument("--coarse-only", type=int, default=0,

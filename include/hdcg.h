@@ -175,6 +175,9 @@ typedef struct {
     int flexible;          /* 1: flexible (Polak-Ribiere) beta; 0: standard PCG beta */
     int maxiter;           /* outer iteration cap */
     double reliable_delta; /* FP64 true-residual update when |r| falls by this factor */
+    int batch;             /* nrhs > 1: 1 solves up to 16 right-hand sides in lockstep (one
+                              launch per step covers all of them, the coarse level reads the
+                              subspace and A once for all); 0 solves them one after another */
 } hdcg_params;
 
 typedef struct {
@@ -191,7 +194,7 @@ typedef struct {
 } hdcg_stats;
 
 /* Fill p with the defaults (A-DEF2, FP32 outer, FP32 sloppy, M_IRS(7, 1.0),
- * coarse tol 0.04, flexible, reliable delta 0.01). */
+ * coarse tol 0.04, flexible, reliable delta 0.01, batched). */
 void hdcg_default_params(hdcg_params* p);
 
 /* Solve H x = b for nrhs right-hand sides to |b - H x| / |b| <= tol (true FP64

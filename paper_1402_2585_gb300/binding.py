@@ -42,7 +42,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int), ("outer_prec", ctypes.c_int), ("sloppy_prec", ctypes.c_int),
                 ("mirs_iter", ctypes.c_int), ("mirs_shift", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxiter", ctypes.c_int), ("flexible", ctypes.c_int), ("maxiter", ctypes.c_int),
-                ("reliable_delta", ctypes.c_double)]
+                ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

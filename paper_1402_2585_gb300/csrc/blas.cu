@@ -125,8 +125,9 @@ void zero_field(Ctx& c, uint4* f, int prec, size_t nf) {
 // reductions
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void k_norm2(const uint4* __restrict__ a, size_t n5, Reduction red) {
+__global__ void k_norm2(const uint4* __restrict__ a, size_t n5, Reduction red, size_t fstride) {
   using R = typename Store<S>::real;
+  a += blockIdx.y * fstride;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (t < n5) {
@@ -161,20 +162,22 @@ __global__ void k_cdot(const uint4* __restrict__ a, const uint4* __restrict__ b,
   grid_reduce<2>(v, red);
 }
 
-Reduction make_reduction(Ctx& c, unsigned grid, int nv, double* result, int accumulate) {
-  c.red_partials.ensure((size_t)grid * nv * sizeof(double) + 64);
+Reduction make_reduction(Ctx& c, unsigned grid, int nv, double* result, int accumulate, int nrhs) {
+  c.red_partials.ensure((size_t)grid * nv * nrhs * sizeof(double) + 64);
   Reduction r;
   r.partials = c.red_partials.as<double>();
   r.ticket = c.red_ticket.as<unsigned>();
   r.result = result;
   r.accumulate = accumulate;
+  r.result_stride = nv;  // NV values per right-hand side, contiguous
   return r;
 }
 
-void norm2(Ctx& c, const uint4* a, int prec, size_t /*n_reals*/, double* result) {
+void norm2(Ctx& c, const uint4* a, int prec, size_t /*n_reals*/, double* result, int nrhs) {
   const unsigned g = blocks_for(c.n5);
-  Reduction r = make_reduction(c, g, 1, result, 0);
-  DISPATCH_PREC(prec, S, { k_norm2<S><<<g, 256, 0, c.stream>>>(a, c.n5, r); });
+  Reduction r = make_reduction(c, g, 1, result, 0, nrhs);
+  const size_t fs = c.field_bytes(prec) / 16;
+  DISPATCH_PREC(prec, S, { k_norm2<S><<<dim3(g, nrhs), 256, 0, c.stream>>>(a, c.n5, r, fs); });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
 }
@@ -234,13 +237,16 @@ __global__ void k_update_xr(uint4* x, const uint4* __restrict__ p, uint4* r, con
 // p = y + beta p ; optional |p|^2 -> red
 template <typename S>
 __global__ void k_update_p(uint4* p, const uint4* __restrict__ y, size_t n5, ScalarRef be, int do_red,
-                           Reduction red) {
+                           Reduction red, size_t fstride) {
   using R = typename Store<S>::real;
+  const int rr = blockIdx.y;
+  p += rr * fstride;
+  y += rr * fstride;
   double beta = 0.0;
   {
-    double n = *be.num;
-    if (be.den1) n -= *be.den1;  // n1 stored in den1 slot for beta
-    const double d = *be.den0;
+    double n = be.num[rr * be.stride];
+    if (be.den1) n -= be.den1[rr * be.stride];  // n1 stored in den1 slot for beta
+    const double d = be.den0[rr];
     beta = d != 0.0 ? n / d : 0.0;
   }
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,8 +271,12 @@ __global__ void k_update_p(uint4* p, const uint4* __restrict__ y, size_t n5, Sca
 // res[0] = Re<a, b>, res[1] = Re<a, c> (c may be null)
 template <typename S>
 __global__ void k_redot2(const uint4* __restrict__ a, const uint4* __restrict__ b, const uint4* __restrict__ cc,
-                         size_t n5, Reduction red) {
+                         size_t n5, Reduction red, size_t fstride) {
   using R = typename Store<S>::real;
+  const size_t ro = blockIdx.y * fstride;
+  a += ro;
+  b += ro;
+  if (cc) cc += ro;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0.0, 0.0};
   if (t < n5) {
@@ -290,9 +300,11 @@ __global__ void k_redot2(const uint4* __restrict__ a, const uint4* __restrict__ 
 
 // hi += lo ; lo = 0
 template <typename Sh, typename Sl>
-__global__ void k_accum_hi(uint4* hi, uint4* lo, size_t n5) {
+__global__ void k_accum_hi(uint4* hi, uint4* lo, size_t n5, size_t fsh, size_t fsl) {
   using Rh = typename Store<Sh>::real;
   using Rl = typename Store<Sl>::real;
+  hi += blockIdx.y * fsh;
+  lo += blockIdx.y * fsl;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n5) return;
   Rh h[24];
@@ -344,12 +356,16 @@ __global__ void k_scale_dev(const uint4* __restrict__ x, uint4* y, size_t n5, co
 // out = s * in with s = sqrt(num / den) (inv: 1 / s), precisions may differ
 template <typename Si, typename So>
 __global__ void k_convert_scaled(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n5,
-                                 const double* num, const double* den, int inv) {
+                                 const double* num, const double* den, int inv, size_t fsi, size_t fso) {
   using Ri = typename Store<Si>::real;
   using Ro = typename Store<So>::real;
+  const int rr = blockIdx.y;
+  in += rr * fsi;
+  out += rr * fso;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n5) return;
-  const double q = (*den > 0.0 && *num > 0.0) ? *num / *den : 1.0;
+  const double nv = num[0], dv = den[rr];
+  const double q = (dv > 0.0 && nv > 0.0) ? nv / dv : 1.0;
   double sc = sqrt(q);
   if (inv) sc = 1.0 / sc;
   Ri v[24];
@@ -362,10 +378,13 @@ __global__ void k_convert_scaled(const uint4* __restrict__ in, uint4* __restrict
 }
 
 void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, const double* num, const double* den,
-                    int inv) {
+                    int inv, int nrhs) {
   const unsigned g = blocks_for(c.n5);
+  const size_t fsi = c.field_bytes(pin) / 16, fso = c.field_bytes(pout) / 16;
   DISPATCH_PREC(pin, Si, {
-    DISPATCH_PREC(pout, So, { k_convert_scaled<Si, So><<<g, 256, 0, c.stream>>>(in, out, c.n5, num, den, inv); });
+    DISPATCH_PREC(pout, So, {
+      k_convert_scaled<Si, So><<<dim3(g, nrhs), 256, 0, c.stream>>>(in, out, c.n5, num, den, inv, fsi, fso);
+    });
   });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
@@ -382,26 +401,33 @@ void update_xr(Ctx& c, int prec_x, uint4* x, int prec, const uint4* p, uint4* r,
   ++c.launches;
 }
 
-void update_p(Ctx& c, int prec, uint4* p, const uint4* y, ScalarRef beta, double* pp_out) {
+void update_p(Ctx& c, int prec, uint4* p, const uint4* y, ScalarRef beta, double* pp_out, int nrhs) {
   const unsigned g = blocks_for(c.n5);
-  Reduction red = make_reduction(c, g, 1, pp_out, 0);
-  DISPATCH_PREC(prec, S, { k_update_p<S><<<g, 256, 0, c.stream>>>(p, y, c.n5, beta, pp_out != nullptr, red); });
+  Reduction red = make_reduction(c, g, 1, pp_out, 0, nrhs);
+  const size_t fs = c.field_bytes(prec) / 16;
+  DISPATCH_PREC(prec, S, {
+    k_update_p<S><<<dim3(g, nrhs), 256, 0, c.stream>>>(p, y, c.n5, beta, pp_out != nullptr, red, fs);
+  });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
 }
 
-void redot2(Ctx& c, int prec, const uint4* a, const uint4* b, const uint4* cc, double* out2) {
+void redot2(Ctx& c, int prec, const uint4* a, const uint4* b, const uint4* cc, double* out2, int nrhs) {
   const unsigned g = blocks_for(c.n5);
-  Reduction red = make_reduction(c, g, 2, out2, 0);
-  DISPATCH_PREC(prec, S, { k_redot2<S><<<g, 256, 0, c.stream>>>(a, b, cc, c.n5, red); });
+  Reduction red = make_reduction(c, g, 2, out2, 0, nrhs);
+  const size_t fs = c.field_bytes(prec) / 16;
+  DISPATCH_PREC(prec, S, { k_redot2<S><<<dim3(g, nrhs), 256, 0, c.stream>>>(a, b, cc, c.n5, red, fs); });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
 }
 
-void accum_hi(Ctx& c, int prec_hi, uint4* hi, int prec_lo, uint4* lo) {
+void accum_hi(Ctx& c, int prec_hi, uint4* hi, int prec_lo, uint4* lo, int nrhs) {
   const unsigned g = blocks_for(c.n5);
+  const size_t fsh = c.field_bytes(prec_hi) / 16, fsl = c.field_bytes(prec_lo) / 16;
   DISPATCH_PREC(prec_hi, Sh, {
-    DISPATCH_PREC(prec_lo, Sl, { k_accum_hi<Sh, Sl><<<g, 256, 0, c.stream>>>(hi, lo, c.n5); });
+    DISPATCH_PREC(prec_lo, Sl, {
+      k_accum_hi<Sh, Sl><<<dim3(g, nrhs), 256, 0, c.stream>>>(hi, lo, c.n5, fsh, fsl);
+    });
   });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;

@@ -40,24 +40,28 @@ struct ScalarRef {
   const double* den0 = nullptr;
   const double* den1 = nullptr;
   double lam = 0.0;
+  int stride = 1;  // right-hand side r reads ptr[r * stride]
 };
 
-Reduction make_reduction(Ctx& c, unsigned grid, int nv, double* result, int accumulate);
+// Reduction of NV values per block (nrhs right-hand sides along grid y); the
+// results of right-hand side r are result[r * nv + i].
+Reduction make_reduction(Ctx& c, unsigned grid, int nv, double* result, int accumulate, int nrhs = 1);
 
 // x += sign_x * alpha p (x may be null); r -= alpha w; rr_out = |r|^2
 void update_xr(Ctx& c, int prec_x, uint4* x, int prec, const uint4* p, uint4* r, const uint4* w,
                ScalarRef alpha, int sign_x, double* rr_out);
 // p = y + beta p; pp_out (may be null) = |p|^2
-void update_p(Ctx& c, int prec, uint4* p, const uint4* y, ScalarRef beta, double* pp_out);
+void update_p(Ctx& c, int prec, uint4* p, const uint4* y, ScalarRef beta, double* pp_out, int nrhs = 1);
 // out2[0] = Re<a, b>, out2[1] = Re<a, cc> (cc may be null)
-void redot2(Ctx& c, int prec, const uint4* a, const uint4* b, const uint4* cc, double* out2);
+void redot2(Ctx& c, int prec, const uint4* a, const uint4* b, const uint4* cc, double* out2, int nrhs = 1);
 // hi += lo; lo = 0
-void accum_hi(Ctx& c, int prec_hi, uint4* hi, int prec_lo, uint4* lo);
+void accum_hi(Ctx& c, int prec_hi, uint4* hi, int prec_lo, uint4* lo, int nrhs = 1);
 // y = a x + b y
 void axpby(Ctx& c, double a, int prec_x, const uint4* x, double b, int prec_y, uint4* y);
 // out = sqrt(num / den)^(inv ? -1 : 1) in, converting precision
+// (den is read per right-hand side: den[r]; num[0] is shared)
 void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, const double* num, const double* den,
-                    int inv);
+                    int inv, int nrhs = 1);
 // y = sqrt(num/den)^(inv ? -1 : 1) x
 void scale_dev(Ctx& c, int prec, const uint4* x, uint4* y, const double* num, const double* den, int inv);
 

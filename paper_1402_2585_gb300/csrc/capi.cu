@@ -95,11 +95,11 @@ int hdcg_create(hdcg_t* h, const int dims[4], int Ls, int antiperiodic_t, void* 
     c->V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
     c->n4 = c->V / 2;
     c->n5 = c->n4 * Ls;
-    c->scalars.ensure(256 * sizeof(double));
-    c->red_ticket.ensure(64);
+    c->scalars.ensure(256 * RMAX * sizeof(double));
+    c->red_ticket.ensure(RMAX * sizeof(unsigned) * 4);
     c->red_partials.ensure(((c->n5 + 255) / 256 + 1024) * 4 * sizeof(double));
-    HDCG_CUDA(cudaMemset(c->scalars.p, 0, 256 * sizeof(double)));
-    HDCG_CUDA(cudaMemset(c->red_ticket.p, 0, 64));
+    HDCG_CUDA(cudaMemset(c->scalars.p, 0, 256 * RMAX * sizeof(double)));
+    HDCG_CUDA(cudaMemset(c->red_ticket.p, 0, RMAX * sizeof(unsigned) * 4));
     dwf_setup_tables(*c);
     HDCG_CUDA(cudaStreamSynchronize(c->stream));
   } catch (const Error& e) {
@@ -169,7 +169,7 @@ int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp)
     c.canon_in.ensure(c.field_bytes(prec));
     c.canon_out.ensure(c.field_bytes(prec));
     canon_to_internal(c, in, prec, c.canon_in.as<uint4>(), prec);
-    double* d = c.scalars.as<double>() + 200;
+    double* d = c.scalars.as<double>() + 200 * RMAX;
     apply_mdagm(c, prec, c.canon_in.as<uint4>(), c.canon_out.as<uint4>(), pHp ? d : nullptr);
     internal_to_canon(c, c.canon_out.as<uint4>(), prec, out, prec);
     if (pHp) {
@@ -319,6 +319,7 @@ void hdcg_default_params(hdcg_params* p) {
   p->flexible = 1;
   p->maxiter = 10000;
   p->reliable_delta = 0.01;
+  p->batch = 1;
 }
 
 int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p, hdcg_stats* st,

@@ -182,13 +182,14 @@ struct GramPhase {
   const int* coords;
 };
 
-template <typename Sx, typename Sy, typename Rt>
+// SAME: Y is X (self Gram matrix): the tile is staged once.
+template <typename Sx, typename Sy, typename Rt, bool SAME = false>
 __global__ void __launch_bounds__(256) k_block_gram(const uint4* X, size_t xstride, int nx, const uint4* Y,
                                                     size_t ystride, int ny, BlockArgs ba, double2* out,
                                                     size_t ostride, GramPhase ph) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Rt* xs = reinterpret_cast<Rt*>(smraw);
-  Rt* ys = xs + (size_t)nx * TROW;
+  Rt* ys = SAME ? xs : xs + (size_t)nx * TROW;
   const size_t b = blockIdx.x;
   const int npairs = nx * ny;
   constexpr int MAXP = (MAX_NVEC * MAX_NVEC + 255) / 256;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256) k_block_gram(const uint4* X, size_t xstri
   for (int tile0 = 0; tile0 < nsites; tile0 += TILE) {
     __syncthreads();
     load_tile<Sx, Rt>(xs, X, xstride, nx, ba, b, tile0);
-    load_tile<Sy, Rt>(ys, Y, ystride, ny, ba, b, tile0);
+    if (!SAME) load_tile<Sy, Rt>(ys, Y, ystride, ny, ba, b, tile0);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < MAXP; ++q) {
@@ -369,11 +370,26 @@ static void launch_gram_t(Ctx& c, const Subspace& s, const uint4* X, int nx, con
 static void block_gram(Ctx& c, const Subspace& s, const uint4* Y, int ny, int yprec, size_t ystride,
                        double2* out, size_t ostride, GramPhase ph) {
   DISPATCH_SUB(s.prec, Sx, {
-    DISPATCH_SUB(yprec, Sy, {
+    DISPATCH_PREC(yprec, Sy, {
       using Rt = typename std::conditional<std::is_same<Sx, f64_t>::value, double, float>::type;
       launch_gram_t<Sx, Sy, Rt>(c, s, s.vecs.as<uint4>(), s.nvec, Y, ny, ystride, out, ostride, ph);
     });
   });
+}
+
+// self Gram matrix of the subspace blocks with FP64 products (orthonormalisation)
+static void block_self_gram(Ctx& c, const Subspace& s, double2* out) {
+  const int n = s.nvec;
+  const size_t stride = s.vec_bytes(c) / 16;
+  const size_t sm = tile_smem<double>(n);
+  DISPATCH_SUB(s.prec, Sx, {
+    auto fn = k_block_gram<Sx, Sx, double, true>;
+    set_smem_limit((const void*)fn, sm);
+    fn<<<(unsigned)s.Vc, 256, sm, c.stream>>>(s.vecs.as<uint4>(), stride, n, s.vecs.as<uint4>(), stride, n,
+                                               block_args(c, s), out, (size_t)n * n, GramPhase{});
+  });
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
 }
 
 void block_orthonormalise(Ctx& c, Subspace& s) {
@@ -383,10 +399,9 @@ void block_orthonormalise(Ctx& c, Subspace& s) {
   T.ensure(s.Vc * n * n * sizeof(double2));
   fail.ensure(sizeof(int));
   HDCG_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int), c.stream));
-  GramPhase noph{};
   const size_t stride = s.vec_bytes(c) / 16;
   for (int round = 0; round < 2; ++round) {
-    block_gram(c, s, s.vecs.as<uint4>(), n, s.prec, stride, G.as<double2>(), (size_t)n * n, noph);
+    block_self_gram(c, s, G.as<double2>());
     k_cholinv<<<(unsigned)((s.Vc + 63) / 64), 64, 0, c.stream>>>(G.as<double2>(), T.as<double2>(), n, s.Vc,
                                                                   fail.as<int>());
     HDCG_CUDA(cudaGetLastError());
@@ -788,6 +803,7 @@ void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec) {
 // loads are in flight per lane.
 constexpr int CGROUPS = 3;
 constexpr int CWARPS = 8;
+template <typename AT> constexpr int vec_width() { return 16 / (int)sizeof(AT); }
 
 template <typename AT, typename R>
 __device__ __forceinline__ void ld_a(const AT* p, R& re, R& im);
@@ -807,7 +823,30 @@ template <> __device__ __forceinline__ void ld_a<__half2, float>(const __half2* 
   im = v.y;
 }
 
-template <typename AT, typename R>
+// 16-byte vector of VJ consecutive complex entries of A (VJ = 16 / sizeof(AT))
+template <typename AT, typename R, int VJ>
+__device__ __forceinline__ void ld_a_vec(const AT* p, R* re, R* im) {
+  if constexpr (VJ == 1) {
+    ld_a<AT, R>(p, re[0], im[0]);
+  } else if constexpr (sizeof(AT) == 8) {  // float2 x 2
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    re[0] = v.x; im[0] = v.y; re[1] = v.z; im[1] = v.w;
+  } else {  // half2 x 4
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    float2 f;
+    f = h2f(v.x); re[0] = f.x; im[0] = f.y;
+    f = h2f(v.y); re[1] = f.x; im[1] = f.y;
+    f = h2f(v.z); re[2] = f.x; im[2] = f.y;
+    f = h2f(v.w); re[3] = f.x; im[3] = f.y;
+  }
+}
+
+// Warp layout: lane = ks * NJ + jp with NJ = n / VJ column groups (jp) and
+// KS = 32 / NJ row subgroups (ks); a lane reads VJ consecutive j of rows
+// k = ks, ks + KS, ... with one 16-byte load per row (for NJ > 32 a lane
+// also takes column group jp + 32).  Row partial sums are combined across
+// the KS subgroups with shuffles, then across warps in shared memory.
+template <typename AT, typename R, int VJ>
 __device__ __forceinline__ void capply_body(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
                                             const typename CV<R>::T* __restrict__ x, typename CV<R>::T* ypart,
                                             size_t nc, double* dot_out) {
@@ -815,47 +854,82 @@ __device__ __forceinline__ void capply_body(const AT* __restrict__ A, const int*
   const size_t a = blockIdx.x / CGROUPS;
   const int g = blockIdx.x % CGROUPS;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int NJ = n / VJ;
+  const int KS = NJ <= 32 ? 32 / NJ : 1;
+  const int ks = NJ <= 32 ? lane / NJ : 0;
+  const int jp0 = NJ <= 32 ? lane % NJ : lane;
+  const bool on0 = ks < KS && jp0 < NJ;
+  const bool on1 = NJ > 32 && lane + 32 < NJ;
   const int l0 = g * 27, l1 = l0 + 27;
-  R sr0 = 0, si0 = 0, sr1 = 0, si1 = 0;   // j = lane, j = lane + 32
-  const int j0 = lane, j1 = lane + 32;
+  R sr[2 * VJ], si[2 * VJ];
+#pragma unroll
+  for (int q = 0; q < 2 * VJ; ++q) sr[q] = si[q] = 0;
   for (int l = l0 + w; l < l1; l += CWARPS) {
     const int nb = __ldg(cnbr + a * 81 + l);
     const AT* blk = A + ((a * 81 + l) * n) * n;
     const typename CV<R>::T* xv = x + (size_t)nb * n;
-    int k = 0;
-    for (; k + 4 <= n; k += 4) {
-      R ar[4], ai[4], br[4], bi[4];
+    int k = ks;
+    for (; k + 3 * KS < n; k += 4 * KS) {
+      R ar[4][2 * VJ], ai[4][2 * VJ];
       typename CV<R>::T xk[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        xk[u] = xv[k + u];
-        ar[u] = ai[u] = br[u] = bi[u] = 0;
-        if (j0 < n) ld_a<AT, R>(blk + (size_t)(k + u) * n + j0, ar[u], ai[u]);
-        if (j1 < n) ld_a<AT, R>(blk + (size_t)(k + u) * n + j1, br[u], bi[u]);
+        xk[u] = xv[k + u * KS];
+#pragma unroll
+        for (int q = 0; q < 2 * VJ; ++q) ar[u][q] = ai[u][q] = 0;
+        if (on0) ld_a_vec<AT, R, VJ>(blk + (size_t)(k + u * KS) * n + jp0 * VJ, ar[u], ai[u]);
+        if (on1) ld_a_vec<AT, R, VJ>(blk + (size_t)(k + u * KS) * n + (jp0 + 32) * VJ, ar[u] + VJ, ai[u] + VJ);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        sr0 += ar[u] * xk[u].x - ai[u] * xk[u].y;
-        si0 += ar[u] * xk[u].y + ai[u] * xk[u].x;
-        sr1 += br[u] * xk[u].x - bi[u] * xk[u].y;
-        si1 += br[u] * xk[u].y + bi[u] * xk[u].x;
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 2 * VJ; ++q) {
+          sr[q] += ar[u][q] * xk[u].x - ai[u][q] * xk[u].y;
+          si[q] += ar[u][q] * xk[u].y + ai[u][q] * xk[u].x;
+        }
+    }
+    for (; k < n; k += KS) {
+      const typename CV<R>::T xk = xv[k];
+      R ar[2 * VJ], ai[2 * VJ];
+#pragma unroll
+      for (int q = 0; q < 2 * VJ; ++q) ar[q] = ai[q] = 0;
+      if (on0) ld_a_vec<AT, R, VJ>(blk + (size_t)k * n + jp0 * VJ, ar, ai);
+      if (on1) ld_a_vec<AT, R, VJ>(blk + (size_t)k * n + (jp0 + 32) * VJ, ar + VJ, ai + VJ);
+#pragma unroll
+      for (int q = 0; q < 2 * VJ; ++q) {
+        sr[q] += ar[q] * xk.x - ai[q] * xk.y;
+        si[q] += ar[q] * xk.y + ai[q] * xk.x;
       }
     }
-    for (; k < n; ++k) {
-      const typename CV<R>::T xk = xv[k];
-      R ar = 0, ai = 0, br = 0, bi = 0;
-      if (j0 < n) ld_a<AT, R>(blk + (size_t)k * n + j0, ar, ai);
-      if (j1 < n) ld_a<AT, R>(blk + (size_t)k * n + j1, br, bi);
-      sr0 += ar * xk.x - ai * xk.y;
-      si0 += ar * xk.y + ai * xk.x;
-      sr1 += br * xk.x - bi * xk.y;
-      si1 += br * xk.y + bi * xk.x;
+  }
+  // combine the KS row subgroups: lanes ks * NJ + jp (same jp) hold partials of the same j
+  if (NJ <= 32) {
+    for (int d = 1; d < KS; d <<= 1) {
+#pragma unroll
+      for (int q = 0; q < VJ; ++q) {
+        const R tr = __shfl_down_sync(FULL_MASK, sr[q], d * NJ);
+        const R ti = __shfl_down_sync(FULL_MASK, si[q], d * NJ);
+        if ((ks & (2 * d - 1)) == 0 && ks + d < KS) {
+          sr[q] += tr;
+          si[q] += ti;
+        }
+      }
     }
   }
-  sre[w][j0] = (double)sr0;
-  sim[w][j0] = (double)si0;
-  sre[w][j1] = (double)sr1;
-  sim[w][j1] = (double)si1;
+  if (ks == 0 && jp0 < NJ) {
+#pragma unroll
+    for (int q = 0; q < VJ; ++q) {
+      sre[w][jp0 * VJ + q] = (double)sr[q];
+      sim[w][jp0 * VJ + q] = (double)si[q];
+    }
+  }
+  if (on1) {
+#pragma unroll
+    for (int q = 0; q < VJ; ++q) {
+      sre[w][(jp0 + 32) * VJ + q] = (double)sr[VJ + q];
+      sim[w][(jp0 + 32) * VJ + q] = (double)si[VJ + q];
+    }
+  }
   __syncthreads();
   double dv = 0.0;
   if (threadIdx.x < n) {
@@ -872,13 +946,13 @@ __device__ __forceinline__ void capply_body(const AT* __restrict__ A, const int*
   *dot_out = dv;
 }
 
-template <typename AT, typename R>
+template <typename AT, typename R, int VJ>
 __global__ void __launch_bounds__(256) k_coarse_apply(const AT* __restrict__ A, const int* __restrict__ cnbr,
                                                       int n, const typename CV<R>::T* __restrict__ x,
                                                       typename CV<R>::T* ypart, size_t nc, int do_red,
                                                       Reduction red) {
   double dv = 0.0;
-  capply_body<AT, R>(A, cnbr, n, x, ypart, nc, &dv);
+  capply_body<AT, R, VJ>(A, cnbr, n, x, ypart, nc, &dv);
   double v[1] = {dv};
   if (do_red) grid_reduce<1>(v, red);
 }
@@ -907,8 +981,12 @@ static void coarse_apply_t(Ctx& c, const Coarse& A, const void* x, void* y, doub
   const unsigned g = (unsigned)(A.Vc * CGROUPS);
   Reduction red{};
   if (xAx) red = make_reduction(c, g, 1, xAx, 0);
-  k_coarse_apply<AT, R><<<g, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, (const V*)x, part.as<V>(),
-                                                 nc, xAx != nullptr, red);
+  if (A.nvec % vec_width<AT>() == 0)
+    k_coarse_apply<AT, R, vec_width<AT>()><<<g, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec,
+                                                                     (const V*)x, part.as<V>(), nc, xAx != nullptr, red);
+  else
+    k_coarse_apply<AT, R, 1><<<g, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, (const V*)x,
+                                                      part.as<V>(), nc, xAx != nullptr, red);
   k_sum_groups<R><<<(unsigned)((nc + 255) / 256), 256, 0, c.stream>>>(part.as<V>(), (V*)y, nc);
   HDCG_CUDA(cudaGetLastError());
   c.launches += 2;
@@ -957,13 +1035,13 @@ __global__ void k_ccg_start(CCtl* ctl, double tol, int maxiter) {
   ctl->done = (ctl->rr[0] == 0.0 || maxiter <= 0) ? 1 : 0;
 }
 
-template <typename AT, typename R>
+template <typename AT, typename R, int VJ>
 __global__ void __launch_bounds__(256) k_ccg_apply(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
                                                    const typename CV<R>::T* __restrict__ p, typename CV<R>::T* wpart,
                                                    size_t nc, const CCtl* ctl, Reduction red) {
   if (ctl->done) return;
   double dv = 0.0;
-  capply_body<AT, R>(A, cnbr, n, p, wpart, nc, &dv);
+  capply_body<AT, R, VJ>(A, cnbr, n, p, wpart, nc, &dv);
   double v[1] = {dv};
   grid_reduce<1>(v, red);
 }
@@ -1037,9 +1115,13 @@ static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol
   while (true) {
     for (int b = 0; b < batch && queued < maxiter; ++b, ++queued) {
       const int par = queued & 1;
-      k_ccg_apply<AT, R><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(
-          A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, p, w, nc, ctl,
-          make_reduction(c, (unsigned)(A.Vc * CGROUPS), 1, &ctl->pAp, 0));
+      const Reduction rd = make_reduction(c, (unsigned)(A.Vc * CGROUPS), 1, &ctl->pAp, 0);
+      if (A.nvec % vec_width<AT>() == 0)
+        k_ccg_apply<AT, R, vec_width<AT>()><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(
+            A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, p, w, nc, ctl, rd);
+      else
+        k_ccg_apply<AT, R, 1><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(),
+                                                                              A.nvec, p, w, nc, ctl, rd);
       k_ccg_update<R><<<gv, 256, 0, c.stream>>>((V*)sol, r, p, w, nc, ctl, par,
                                                 make_reduction(c, gv, 1, &ctl->rr[par ^ 1], 0));
       k_ccg_p<R><<<gv, 256, 0, c.stream>>>(p, r, nc, ctl, par, maxiter);
@@ -1173,8 +1255,12 @@ static void coarse_apply_noalloc_t(Ctx& c, const Coarse& A, const void* x64, voi
     x = xs;
     y = ys;
   }
-  k_coarse_apply<AT, R><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, x,
-                                                                          part, nc, 0, Reduction{});
+  if (A.nvec % vec_width<AT>() == 0)
+    k_coarse_apply<AT, R, vec_width<AT>()><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(
+        A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, x, part, nc, 0, Reduction{});
+  else
+    k_coarse_apply<AT, R, 1><<<(unsigned)(A.Vc * CGROUPS), 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(),
+                                                                              A.nvec, x, part, nc, 0, Reduction{});
   k_sum_groups<R><<<gv, 256, 0, c.stream>>>(part, y, nc);
   c.launches += 2;
   if (sizeof(V) != sizeof(double2)) {
@@ -1194,6 +1280,399 @@ void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64) {
   if (A.prec == HDCG_F64) coarse_apply_noalloc_t<double2, double>(c, A, x64, y64);
   else if (A.prec == HDCG_F32) coarse_apply_noalloc_t<float2, float>(c, A, x64, y64);
   else coarse_apply_noalloc_t<__half2, float>(c, A, x64, y64);
+}
+
+
+// ---------------------------------------------------------------------------
+// several right-hand sides (the batched solver).  Coarse vectors of R
+// right-hand sides are stored [a][k][r] (right-hand side fastest).
+// ---------------------------------------------------------------------------
+
+// c[a][k][r] = <phi_k^a, v_r> for R fields v (one Gram pass reads phi once)
+void restrict_multi(Ctx& c, const Subspace& s, const uint4* v, int vprec, int R, void* cvec, int cprec) {
+  const size_t nc = s.Vc * s.nvec * (size_t)R;
+  DevMem G;
+  G.ensure(nc * sizeof(double2));
+  block_gram(c, s, v, R, vprec, c.field_bytes(vprec) / 16, G.as<double2>(), (size_t)s.nvec * R, GramPhase{});
+  cvec_convert(c, G.p, HDCG_F64, cvec, cprec, nc);
+}
+
+// out_r = add_r + sum_k c[b][k][r] phi_k  (tile of all vectors in shared memory)
+template <typename Sp, typename So, typename Rt>
+__global__ void __launch_bounds__(256) k_prolong_multi(const uint4* phi, size_t pstride, int n, BlockArgs ba,
+                                                       const typename CV<Rt>::T* __restrict__ cv, int R,
+                                                       uint4* out, const uint4* add, size_t ostride) {
+  using Ro = typename Store<So>::real;
+  constexpr int C = Store<So>::chunks, P = Store<So>::per_chunk;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Rt* xs = reinterpret_cast<Rt*>(smraw);
+  Rt* cs = xs + (size_t)n * TROW;    // [k][r] complex
+  const size_t b = blockIdx.x;
+  for (int q = threadIdx.x; q < n * R; q += blockDim.x) {
+    const typename CV<Rt>::T v = cv[b * n * R + q];
+    cs[2 * q] = v.x;
+    cs[2 * q + 1] = v.y;
+  }
+  const int nsites = ba.spb * ba.Ls;
+  const int units = R * TILE * C;
+  for (int tile0 = 0; tile0 < nsites; tile0 += TILE) {
+    __syncthreads();
+    load_tile<Sp, Rt>(xs, phi, pstride, n, ba, b, tile0);
+    __syncthreads();
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int t = u % TILE;
+      const int ch = (u / TILE) % C;
+      const int r = u / (C * TILE);
+      Rt o[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) o[i] = 0;
+      for (int k = 0; k < n; ++k) {
+        const Rt cr = cs[2 * (k * R + r)], ci = cs[2 * (k * R + r) + 1];
+        const Rt* xr = xs + k * TROW + t * 24 + ch * P;
+#pragma unroll
+        for (int i = 0; i < P; i += 2) {
+          o[i] += cr * xr[i] - ci * xr[i + 1];
+          o[i + 1] += cr * xr[i + 1] + ci * xr[i];
+        }
+      }
+      const size_t site5 = block_site5(ba, b, tile0 + t);
+      if (add) {
+        Ro av[P];
+        unpack(So{}, __ldg(add + r * ostride + ch * ba.n5 + site5), av);
+#pragma unroll
+        for (int i = 0; i < P; ++i) o[i] += (Rt)av[i];
+      }
+      Ro w[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) w[i] = (Ro)o[i];
+      out[r * ostride + ch * ba.n5 + site5] = pack(So{}, w);
+    }
+  }
+}
+
+void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R, uint4* out, int oprec,
+                   const uint4* add) {
+  HDCG_REQUIRE((cprec == HDCG_F64) == (s.prec == HDCG_F64), HDCG_ERR_ARG,
+               "coarse vectors are FP64 exactly when the subspace is FP64");
+  const int n = s.nvec;
+  const size_t pstride = s.vec_bytes(c) / 16, ostride = c.field_bytes(oprec) / 16;
+  DISPATCH_SUB(s.prec, Sp, {
+    DISPATCH_PREC(oprec, So, {
+      using Rt = typename std::conditional<std::is_same<Sp, f64_t>::value, double, float>::type;
+      const size_t sm = tile_smem<Rt>(n) + (size_t)n * R * 2 * sizeof(Rt);
+      auto fn = k_prolong_multi<Sp, So, Rt>;
+      set_smem_limit((const void*)fn, sm);
+      fn<<<(unsigned)s.Vc, 256, sm, c.stream>>>(s.vecs.as<uint4>(), pstride, n, block_args(c, s),
+                                                 (const typename CV<Rt>::T*)cvec, R, out, add, ostride);
+    });
+  });
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+}
+
+// Y[a][j][r] = sum_l sum_k A[a][l][k][j] X[a+l][k][r] for R right-hand sides.
+// Same warp layout as capply_body; every lane keeps VJ x R accumulators and
+// reads A once for all right-hand sides.  Per-rhs partial dots Re<X_r, Y_r>
+// of this CGROUPS slice go to dot_out[r].
+template <typename AT, typename R_, int VJ>
+__device__ __forceinline__ void capply_multi_body(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
+                                                  int R, const typename CV<R_>::T* __restrict__ x,
+                                                  typename CV<R_>::T* ypart, size_t nc, double* dot_out,
+                                                  float2* sred) {
+  using V = typename CV<R_>::T;
+  const size_t a = blockIdx.x / CGROUPS;
+  const int g = blockIdx.x % CGROUPS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int NJ = n / VJ;
+  const int KS = NJ <= 32 ? 32 / NJ : 1;
+  const int ks = NJ <= 32 ? lane / NJ : 0;
+  const int jp0 = NJ <= 32 ? lane % NJ : lane;
+  const bool on0 = ks < KS && jp0 < NJ;
+  const bool on1 = NJ > 32 && lane + 32 < NJ;
+  const int l0 = g * 27, l1 = l0 + 27;
+  R_ sr[2 * VJ][RMAX], si[2 * VJ][RMAX];
+#pragma unroll
+  for (int q = 0; q < 2 * VJ; ++q)
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) sr[q][r] = si[q][r] = 0;
+  for (int l = l0 + w; l < l1; l += CWARPS) {
+    const int nb = __ldg(cnbr + a * 81 + l);
+    const AT* blk = A + ((a * 81 + l) * n) * n;
+    const V* xv = x + (size_t)nb * n * R;
+    for (int k = ks; k < n; k += KS) {
+      R_ ar[2 * VJ], ai[2 * VJ];
+#pragma unroll
+      for (int q = 0; q < 2 * VJ; ++q) ar[q] = ai[q] = 0;
+      if (on0) ld_a_vec<AT, R_, VJ>(blk + (size_t)k * n + jp0 * VJ, ar, ai);
+      if (on1) ld_a_vec<AT, R_, VJ>(blk + (size_t)k * n + (jp0 + 32) * VJ, ar + VJ, ai + VJ);
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r < R) {
+          const V xk = xv[(size_t)k * R + r];
+#pragma unroll
+          for (int q = 0; q < 2 * VJ; ++q) {
+            sr[q][r] += ar[q] * xk.x - ai[q] * xk.y;
+            si[q][r] += ar[q] * xk.y + ai[q] * xk.x;
+          }
+        }
+      }
+    }
+  }
+  if (NJ <= 32) {
+    for (int d = 1; d < KS; d <<= 1) {
+#pragma unroll
+      for (int q = 0; q < VJ; ++q)
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+          const R_ tr = __shfl_down_sync(FULL_MASK, sr[q][r], d * NJ);
+          const R_ ti = __shfl_down_sync(FULL_MASK, si[q][r], d * NJ);
+          if ((ks & (2 * d - 1)) == 0 && ks + d < KS) {
+            sr[q][r] += tr;
+            si[q][r] += ti;
+          }
+        }
+    }
+  }
+  // sred: [CWARPS][n][R] float2
+  if (ks == 0 && jp0 < NJ)
+#pragma unroll
+    for (int q = 0; q < VJ; ++q)
+      for (int r = 0; r < R; ++r)
+        sred[((size_t)w * n + jp0 * VJ + q) * R + r] = make_float2((float)sr[q][r], (float)si[q][r]);
+  if (on1)
+#pragma unroll
+    for (int q = 0; q < VJ; ++q)
+      for (int r = 0; r < R; ++r)
+        sred[((size_t)w * n + (jp0 + 32) * VJ + q) * R + r] = make_float2((float)sr[VJ + q][r], (float)si[VJ + q][r]);
+  __syncthreads();
+  for (int r = 0; r < RMAX; ++r) dot_out[r] = 0.0;
+  for (int o = threadIdx.x; o < n * R; o += blockDim.x) {
+    float tr = 0, ti = 0;
+#pragma unroll
+    for (int q = 0; q < CWARPS; ++q) {
+      const float2 v = sred[(size_t)q * n * R + o];
+      tr += v.x;
+      ti += v.y;
+    }
+    ypart[g * nc + a * n * R + o] = {(R_)tr, (R_)ti};
+    const V xa = x[a * n * R + o];
+    const int r = o % R;
+#pragma unroll
+    for (int rr = 0; rr < RMAX; ++rr)
+      if (rr == r) dot_out[rr] += (double)xa.x * tr + (double)xa.y * ti;
+  }
+}
+
+struct CCtlM {
+  double rr[2][RMAX];
+  double pAp[RMAX];
+  double stop[RMAX];
+  int done[RMAX];
+  int iter;
+  int all_done;
+};
+
+template <typename AT, typename R_, int VJ>
+__global__ void __launch_bounds__(256) k_capply_multi(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
+                                                      int R, const typename CV<R_>::T* __restrict__ x,
+                                                      typename CV<R_>::T* ypart, size_t nc, const CCtlM* ctl,
+                                                      Reduction red) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (ctl && ctl->all_done) return;
+  double dot[RMAX];
+  capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<float2*>(smraw));
+  if (red.result) grid_reduce<RMAX>(dot, red);
+}
+
+template <typename R_>
+__global__ void k_ccgm_init(const typename CV<R_>::T* rhs, typename CV<R_>::T* x, typename CV<R_>::T* r,
+                            typename CV<R_>::T* p, size_t ne, int R, Reduction red) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // coarse site-vector (a, k)
+  double v[RMAX];
+#pragma unroll
+  for (int q = 0; q < RMAX; ++q) v[q] = 0.0;
+  if (t < ne) {
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q) {
+      if (q < R) {
+        const typename CV<R_>::T b = rhs[t * R + q];
+        x[t * R + q] = {0, 0};
+        r[t * R + q] = b;
+        p[t * R + q] = b;
+        v[q] = (double)b.x * b.x + (double)b.y * b.y;
+      }
+    }
+  }
+  grid_reduce<RMAX>(v, red);
+}
+
+__global__ void k_ccgm_start(CCtlM* ctl, int R, double tol, int maxiter) {
+  int all = 1;
+  for (int q = 0; q < R; ++q) {
+    ctl->stop[q] = tol * tol * ctl->rr[0][q];
+    ctl->done[q] = (ctl->rr[0][q] == 0.0 || maxiter <= 0) ? 1 : 0;
+    all &= ctl->done[q];
+  }
+  ctl->iter = 0;
+  ctl->all_done = all;
+}
+
+template <typename R_>
+__global__ void k_ccgm_update(typename CV<R_>::T* x, typename CV<R_>::T* r, const typename CV<R_>::T* p,
+                              const typename CV<R_>::T* w, size_t ne, int R, size_t nc, const CCtlM* ctl, int par,
+                              Reduction red) {
+  if (ctl->all_done) return;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[RMAX];
+#pragma unroll
+  for (int q = 0; q < RMAX; ++q) v[q] = 0.0;
+  if (t < ne) {
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q) {
+      if (q < R) {
+        const double pap = ctl->pAp[q];
+        const R_ al = (R_)((!ctl->done[q] && pap > 0) ? ctl->rr[par][q] / pap : 0.0);
+        const size_t e = t * R + q;
+        typename CV<R_>::T xv = x[e], rv = r[e];
+        const typename CV<R_>::T pv = p[e];
+        typename CV<R_>::T wv = w[e];
+#pragma unroll
+        for (int g = 1; g < CGROUPS; ++g) {
+          wv.x += w[g * nc + e].x;
+          wv.y += w[g * nc + e].y;
+        }
+        xv.x += al * pv.x;
+        xv.y += al * pv.y;
+        rv.x -= al * wv.x;
+        rv.y -= al * wv.y;
+        x[e] = xv;
+        r[e] = rv;
+        v[q] = (double)rv.x * rv.x + (double)rv.y * rv.y;
+      }
+    }
+  }
+  grid_reduce<RMAX>(v, red);
+}
+
+template <typename R_>
+__global__ void k_ccgm_p(typename CV<R_>::T* p, const typename CV<R_>::T* r, size_t ne, int R, CCtlM* ctl, int par,
+                         int maxiter) {
+  if (ctl->all_done) return;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ne) {
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q) {
+      if (q < R && !ctl->done[q]) {
+        const double ro = ctl->rr[par][q], rn = ctl->rr[par ^ 1][q];
+        const R_ beta = (R_)(ro > 0 ? rn / ro : 0.0);
+        const size_t e = t * R + q;
+        typename CV<R_>::T pv = p[e];
+        const typename CV<R_>::T rv = r[e];
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        p[e] = pv;
+      }
+    }
+  }
+}
+
+// convergence bookkeeping after an iteration (one thread; ordered after k_ccgm_p)
+__global__ void k_ccgm_check(CCtlM* ctl, int R, int par, int maxiter) {
+  if (ctl->all_done) return;
+  const int it = ctl->iter + 1;
+  ctl->iter = it;
+  int all = 1;
+  for (int q = 0; q < R; ++q) {
+    const double rn = ctl->rr[par ^ 1][q];
+    if (!ctl->done[q] && (rn <= ctl->stop[q] || it >= maxiter || !(rn == rn))) ctl->done[q] = 1;
+    all &= ctl->done[q];
+  }
+  ctl->all_done = all;
+}
+
+template <typename AT, typename R_>
+static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
+  using V = typename CV<R_>::T;
+  const size_t ne = A.Vc * A.nvec;   // coarse site-vector elements per right-hand side
+  const size_t nc = ne * R;
+  A.work.ensure((2 + CGROUPS) * nc * sizeof(V));
+  A.ctl.ensure(sizeof(CCtlM));
+  V* r = A.work.as<V>();
+  V* p = r + nc;
+  V* w = p + nc;
+  CCtlM* ctl = A.ctl.as<CCtlM>();
+  const unsigned ge = (unsigned)((ne + 255) / 256);
+  const unsigned ga = (unsigned)(A.Vc * CGROUPS);
+  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(float2);
+  const bool vec = A.nvec % vec_width<AT>() == 0;
+  auto fn = vec ? k_capply_multi<AT, R_, vec_width<AT>()> : k_capply_multi<AT, R_, 1>;
+  set_smem_limit((const void*)fn, sm);
+  k_ccgm_init<R_><<<ge, 256, 0, c.stream>>>((const V*)rhs, (V*)sol, r, p, ne, R,
+                                            make_reduction(c, ge, RMAX, &ctl->rr[0][0], 0));
+  k_ccgm_start<<<1, 1, 0, c.stream>>>(ctl, R, tol, maxiter);
+  c.launches += 2;
+  int queued = 0;
+  int batch = std::max(1, A.last_iters);
+  CCtlM h{};
+  while (true) {
+    for (int bq = 0; bq < batch && queued < maxiter; ++bq, ++queued) {
+      const int par = queued & 1;
+      fn<<<ga, 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, p, w, nc, ctl,
+                                    make_reduction(c, ga, RMAX, &ctl->pAp[0], 0));
+      k_ccgm_update<R_><<<ge, 256, 0, c.stream>>>((V*)sol, r, p, w, ne, R, nc, ctl, par,
+                                                  make_reduction(c, ge, RMAX, &ctl->rr[par ^ 1][0], 0));
+      k_ccgm_p<R_><<<ge, 256, 0, c.stream>>>(p, r, ne, R, ctl, par, maxiter);
+      k_ccgm_check<<<1, 1, 0, c.stream>>>(ctl, R, par, maxiter);
+      c.launches += 4;
+    }
+    HDCG_CUDA(cudaGetLastError());
+    HDCG_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(CCtlM), cudaMemcpyDeviceToHost, c.stream));
+    HDCG_CUDA(cudaStreamSynchronize(c.stream));
+    if (h.all_done || queued >= maxiter) break;
+    batch = 2;
+  }
+  A.last_iters = std::max(1, h.iter);
+  return h.iter;
+}
+
+int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
+  HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  if (A.prec == HDCG_F64) return coarse_cg_multi_t<double2, double>(c, A, R, rhs, sol, tol, maxiter);
+  if (A.prec == HDCG_F32) return coarse_cg_multi_t<float2, float>(c, A, R, rhs, sol, tol, maxiter);
+  return coarse_cg_multi_t<__half2, float>(c, A, R, rhs, sol, tol, maxiter);
+}
+
+// Y = A X for R right-hand sides (canonical [a][k][r] complex double in and out)
+template <typename AT, typename R_>
+static void coarse_apply_multi_t(Ctx& c, const Coarse& A, int R, const void* x, void* y) {
+  using V = typename CV<R_>::T;
+  const size_t nc = A.Vc * A.nvec * (size_t)R;
+  DevMem tmp;
+  tmp.ensure((2 + CGROUPS) * nc * sizeof(V));
+  V* xi = tmp.as<V>();
+  V* yi = xi + nc;
+  V* part = yi + nc;
+  const int vp = A.vec_prec();
+  cvec_convert(c, x, HDCG_F64, xi, vp, nc);
+  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(float2);
+  const bool vec = A.nvec % vec_width<AT>() == 0;
+  auto fn = vec ? k_capply_multi<AT, R_, vec_width<AT>()> : k_capply_multi<AT, R_, 1>;
+  set_smem_limit((const void*)fn, sm);
+  Reduction none{};
+  fn<<<(unsigned)(A.Vc * CGROUPS), 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, xi, part, nc,
+                                                         nullptr, none);
+  k_sum_groups<R_><<<(unsigned)((nc + 255) / 256), 256, 0, c.stream>>>(part, yi, nc);
+  c.launches += 2;
+  cvec_convert(c, yi, vp, y, HDCG_F64, nc);
+  HDCG_CUDA(cudaGetLastError());
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void coarse_apply_multi(Ctx& c, const Coarse& A, int R, const void* x, void* y) {
+  HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  if (A.prec == HDCG_F64) coarse_apply_multi_t<double2, double>(c, A, R, x, y);
+  else if (A.prec == HDCG_F32) coarse_apply_multi_t<float2, float>(c, A, R, x, y);
+  else coarse_apply_multi_t<__half2, float>(c, A, R, x, y);
 }
 
 }  // namespace hdcg

@@ -66,6 +66,12 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
 size_t coarse_apply_noalloc_bytes(const Coarse& A);
 // y = A x on canonical complex double coarse vectors (device) without allocating
 void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64);
+// several right-hand sides: coarse vectors [a][k][r]
+void restrict_multi(Ctx& c, const Subspace& s, const uint4* v, int vprec, int R, void* cvec, int cprec);
+void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R, uint4* out, int oprec,
+                   const uint4* add);
+int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+void coarse_apply_multi(Ctx& c, const Coarse& A, int R, const void* x, void* y);
 // canonical export of A (complex double [Vc][81][j][k], host)
 void coarse_export(Ctx& c, const Coarse& A, void* host);
 

@@ -169,22 +169,30 @@ __device__ void block_sum(double (&v)[NV]) {
   }
 }
 
+// Several right-hand sides reduce independently: the grid's y index selects
+// the right-hand side (its own partials, ticket and result, result_stride
+// doubles apart); one right-hand side is gridDim.y = 1.
 struct Reduction {
-  double* partials;     // >= NV * gridDim.x doubles
-  unsigned* ticket;     // zero between uses
-  double* result;       // NV doubles
+  double* partials;     // >= NV * gridDim.x * gridDim.y doubles
+  unsigned* ticket;     // gridDim.y tickets, zero between uses
+  double* result;       // NV doubles per right-hand side
   int accumulate;       // 1: result += total, 0: result = total
+  int result_stride;    // doubles between the results of consecutive right-hand sides
 };
 
 template <int NV>
 __device__ void grid_reduce(double (&v)[NV], const Reduction& red) {
   block_sum<NV>(v);
   __shared__ bool last;
+  const unsigned y = blockIdx.y;
+  double* partials = red.partials + (size_t)NV * gridDim.x * y;
+  unsigned* ticket = red.ticket + y;
+  double* result = red.result + (size_t)red.result_stride * y;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) red.partials[NV * blockIdx.x + i] = v[i];
+    for (int i = 0; i < NV; ++i) partials[NV * blockIdx.x + i] = v[i];
     __threadfence();
-    unsigned t = atomicAdd(red.ticket, 1u);
+    unsigned t = atomicAdd(ticket, 1u);
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
@@ -195,12 +203,12 @@ __device__ void grid_reduce(double (&v)[NV], const Reduction& red) {
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)red.partials)[NV * b + i];
+    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[NV * b + i];
   block_sum<NV>(acc);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) red.result[i] = red.accumulate ? red.result[i] + acc[i] : acc[i];
-    *red.ticket = 0;
+    for (int i = 0; i < NV; ++i) result[i] = red.accumulate ? result[i] + acc[i] : acc[i];
+    *ticket = 0;
   }
 }
 

@@ -125,8 +125,8 @@ struct Ctx {
   std::string err;
 
   size_t field_bytes(int prec) const { return n5 * 24 * bytes_per_real(prec); }
-  uint4* scratch(int prec, int i) {
-    scratch_f[prec][i].ensure(field_bytes(prec));
+  uint4* scratch(int prec, int i, int nfields = 1) {
+    scratch_f[prec][i].ensure(field_bytes(prec) * nfields);
     return scratch_f[prec][i].as<uint4>();
   }
 };
@@ -148,7 +148,14 @@ struct HopEpi {
   const double* al_den0 = nullptr;
   const double* al_den1 = nullptr;
   double al_lam = 0.0;
+  // several right-hand sides: nrhs fields fstride granules apart, scalars per rhs
+  int nrhs = 1;
+  size_t fstride = 0;
+  const int* mask = nullptr;
 };
+
+// device scalars: 256 slots of RMAX doubles (one per right-hand side)
+constexpr int RMAX = 16;
 
 void dwf_setup_tables(Ctx& c);
 void dwf_upload_gauge(Ctx& c, const void* U, bool on_device);
@@ -166,7 +173,10 @@ void apply_mdagm(Ctx& c, int prec, const uint4* in, uint4* out, double* mpc_norm
 // alpha = *al_num / (*pw + shift * *pp); r -= alpha w; x += alpha p;
 // *pw <- |Mpc p|^2 (pass B), *rr_out <- |r|^2 (pass D).
 void apply_mdagm_cg(Ctx& c, int prec, const uint4* p, double shift, uint4* x, uint4* r, const double* al_num,
-                    const double* pw, const double* pp, double* rr_out);
+                    const double* pw, const double* pp, double* rr_out, int nrhs = 1, const int* mask = nullptr);
+// out_r = sD * H in_r + lam * extra_r for nrhs consecutive fields; mpc_norm2[r] = |Mpc in_r|^2
+void apply_mdagm_multi(Ctx& c, int prec, int nrhs, const uint4* in, uint4* out, double* mpc_norm2, double sD,
+                       double lam, const uint4* extra);
 
 // ---------------------------------------------------------------------------
 // fields and BLAS-1 (blas.cu); all reductions accumulate in FP64
@@ -178,7 +188,7 @@ void internal_to_canon(Ctx& c, const uint4* in, int prec, void* canon, int canon
 void convert_field(Ctx& c, const uint4* in, int pin, uint4* out, int pout, size_t nfields = 1);
 void zero_field(Ctx& c, uint4* f, int prec, size_t nfields = 1);
 // result[0] = |a|^2
-void norm2(Ctx& c, const uint4* a, int prec, size_t n_reals, double* result);
+void norm2(Ctx& c, const uint4* a, int prec, size_t n_reals, double* result, int nrhs = 1);
 // result[0:2] = <a, b> (complex)
 void cdot(Ctx& c, const uint4* a, const uint4* b, int prec, size_t n_reals, double* result);
 

@@ -173,7 +173,7 @@ static double hop_bytes(const Ctx& c, int pass, int prec, bool extra) {
   return (double)c.n5 * (reals_field * fb + 8.0 * 18.0 * lb / c.Ls);
 }
 
-static void dispatch_hop(int prec, int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st) {
+static void dispatch_hop(int prec, int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st) {
   switch (prec) {
     case HDCG_F64: launch_hop_f64(v, pass, mob, a, grid, st); break;
     case HDCG_F32: launch_hop_f32(v, pass, mob, a, grid, st); break;
@@ -187,7 +187,7 @@ static void dispatch_hop(int prec, int v, int pass, bool mob, const HopArgs& a, 
 // Hop autotuner: the first launch of a (precision, pass, fused-CG) combination
 // times every register-budget variant on scratch fields (never on the
 // caller's data, so in-place CG updates are not repeated) and keeps the fastest.
-static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, unsigned grid) {
+static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, dim3 grid) {
   const int key = ((prec * 4 + pass) * 2 + (a.cg_r ? 1 : 0)) * 2 + (a.do_red ? 1 : 0);
   auto it = c.hop_tuned.find(key);
   if (it != c.hop_tuned.end()) return it->second;
@@ -197,6 +197,9 @@ static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, u
   }
   // scratch copies: inputs are whatever the scratch slots hold (only timing matters)
   HopArgs t = a;
+  t.fstride = 0;
+  t.al_mask = nullptr;
+  grid.y = 1;
   uint4* s0 = c.scratch(prec, 20);
   uint4* s1 = c.scratch(prec, 21);
   uint4* s2 = c.scratch(prec, 22);
@@ -214,7 +217,7 @@ static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, u
     t.cg_x = s3;
     t.cg_p = s0;
   }
-  if (a.do_red) t.red.result = c.scalars.as<double>() + 250;
+  if (a.do_red) t.red.result = c.scalars.as<double>() + 250 * RMAX;
   cudaEvent_t e0, e1;
   HDCG_CUDA(cudaEventCreate(&e0));
   HDCG_CUDA(cudaEventCreate(&e1));
@@ -271,24 +274,29 @@ void launch_hop(Ctx& c, int pass, int prec, const uint4* in, const uint4* in2, u
   a.al_den0 = epi.al_den0;
   a.al_den1 = epi.al_den1;
   a.al_lam = epi.al_lam;
+  a.fstride = epi.nrhs > 1 ? epi.fstride : 0;
+  a.al_mask = epi.mask;
   const unsigned grid = (unsigned)((c.n5 + 255) / 256);
+  HDCG_REQUIRE(epi.nrhs >= 1 && epi.nrhs <= RMAX, HDCG_ERR_ARG, "1 <= right-hand sides <= 16");
   a.do_red = red_result != nullptr;
   if (a.do_red) {
-    c.red_partials.ensure((size_t)grid * 4 * sizeof(double));
+    c.red_partials.ensure((size_t)grid * 4 * epi.nrhs * sizeof(double));
     a.red.partials = c.red_partials.as<double>();
     a.red.ticket = c.red_ticket.as<unsigned>();
     a.red.result = red_result;
     a.red.accumulate = accumulate;
+    a.red.result_stride = 1;
   }
   const bool mob = c.co.c != 0.0;
-  const int v = hop_variant(c, prec, pass, mob, a, grid);
+  const dim3 grid2(grid, (unsigned)epi.nrhs);
+  const int v = hop_variant(c, prec, pass, mob, a, grid2);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (c.prof.on) {
     HDCG_CUDA(cudaEventCreate(&ev0));
     HDCG_CUDA(cudaEventCreate(&ev1));
     HDCG_CUDA(cudaEventRecord(ev0, c.stream));
   }
-  dispatch_hop(prec, v, pass, mob, a, grid, c.stream);
+  dispatch_hop(prec, v, pass, mob, a, grid2, c.stream);
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
   if (c.prof.on) {
@@ -296,8 +304,9 @@ void launch_hop(Ctx& c, int pass, int prec, const uint4* in, const uint4* in2, u
     c.prof.pending.push_back(ev0);
     c.prof.pending.push_back(ev1);
     c.prof.pending_prec.push_back(prec);
-    c.prof.bytes[prec] += hop_bytes(c, pass, prec, epi.extra != nullptr) +
-                          (epi.cg_r ? (double)c.n5 * 24 * bytes_per_real(prec) * (epi.extra ? 4.0 : 5.0) : 0.0);
+    c.prof.bytes[prec] += epi.nrhs * (hop_bytes(c, pass, prec, epi.extra != nullptr) +
+                                      (epi.cg_r ? (double)c.n5 * 24 * bytes_per_real(prec) * (epi.extra ? 4.0 : 5.0)
+                                                : 0.0));
   }
 }
 
@@ -313,13 +322,17 @@ void apply_mpc(Ctx& c, int prec, const uint4* in, uint4* out, int dagger, double
 }
 
 void apply_mdagm_cg(Ctx& c, int prec, const uint4* p, double shift, uint4* x, uint4* r, const double* al_num,
-                    const double* pw, const double* pp, double* rr_out) {
-  uint4* t = c.scratch(prec, 0);
-  uint4* chi = c.scratch(prec, 1);
-  launch_hop(c, PASS_A, prec, p, nullptr, t, HopEpi{}, nullptr, 0);
-  launch_hop(c, PASS_B, prec, t, p, chi, HopEpi{}, const_cast<double*>(pw), 0);
-  launch_hop(c, PASS_C, prec, chi, nullptr, t, HopEpi{}, nullptr, 0);
-  HopEpi e;
+                    const double* pw, const double* pp, double* rr_out, int nrhs, const int* mask) {
+  uint4* t = c.scratch(prec, 0, nrhs);
+  uint4* chi = c.scratch(prec, 1, nrhs);
+  HopEpi m;
+  m.nrhs = nrhs;
+  m.fstride = c.field_bytes(prec) / 16;
+  launch_hop(c, PASS_A, prec, p, nullptr, t, m, nullptr, 0);
+  launch_hop(c, PASS_B, prec, t, p, chi, m, const_cast<double*>(pw), 0);
+  launch_hop(c, PASS_C, prec, chi, nullptr, t, m, nullptr, 0);
+  HopEpi e = m;
+  e.mask = mask;
   e.lam = shift;
   e.extra = shift != 0.0 ? p : nullptr;
   e.cg_x = x;
@@ -330,6 +343,23 @@ void apply_mdagm_cg(Ctx& c, int prec, const uint4* p, double shift, uint4* x, ui
   e.al_den1 = shift != 0.0 ? pp : nullptr;
   e.al_lam = shift;
   launch_hop(c, PASS_D, prec, t, chi, nullptr, e, rr_out, 0);
+}
+
+void apply_mdagm_multi(Ctx& c, int prec, int nrhs, const uint4* in, uint4* out, double* mpc_norm2, double sD,
+                       double lam, const uint4* extra) {
+  uint4* t = c.scratch(prec, 0, nrhs);
+  uint4* chi = c.scratch(prec, 1, nrhs);
+  HopEpi m;
+  m.nrhs = nrhs;
+  m.fstride = c.field_bytes(prec) / 16;
+  launch_hop(c, PASS_A, prec, in, nullptr, t, m, nullptr, 0);
+  launch_hop(c, PASS_B, prec, t, in, chi, m, mpc_norm2, 0);
+  launch_hop(c, PASS_C, prec, chi, nullptr, t, m, nullptr, 0);
+  HopEpi e = m;
+  e.sD = sD;
+  e.lam = lam;
+  e.extra = extra;
+  launch_hop(c, PASS_D, prec, t, chi, out, e, nullptr, 0);
 }
 
 void apply_mdagm(Ctx& c, int prec, const uint4* in, uint4* out, double* mpc_norm2, double sD,

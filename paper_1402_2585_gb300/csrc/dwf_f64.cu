@@ -2,7 +2,7 @@
 #include "dwf_kernels.cuh"
 
 namespace hdcg {
-void launch_hop_f64(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st) {
+void launch_hop_f64(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st) {
   launch_hop_variant<f64_t>(v, pass, mob, a, grid, st);
 }
 }  // namespace hdcg

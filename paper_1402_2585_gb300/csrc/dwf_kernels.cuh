@@ -31,6 +31,10 @@ struct HopArgs {
   const double* al_den0;
   const double* al_den1;
   double al_lam;
+  // several right-hand sides (grid y): fields fstride granules apart, the
+  // fused-CG scalars of right-hand side r at al_*[r]; al_mask[r] == 0 freezes r
+  size_t fstride;
+  const int* al_mask;
 };
 
 // ------------------------------------------------------------------------------
@@ -226,11 +230,12 @@ template <> struct LinkOf<bf16t_t> { using T = __nv_bfloat162; };
 // backward (x - mu, projector 1 + SF g); the two neighbour spinors and links are
 // loaded before either is used so that their loads overlap.
 template <typename St, typename R, typename LT, int MU, int SF, bool KIN>
-__device__ __forceinline__ void hop_pair(const HopArgs& a, const int* nbv, const uint4* lk, int s, R* acc) {
+__device__ __forceinline__ void hop_pair(const HopArgs& a, const uint4* in, const int* nbv, const uint4* lk, int s,
+                                         R* acc) {
   constexpr int LG = LinkGran<LT>::g;
   R pf[24], pb[24];
-  load_spinor<St, R>(a.in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
-  load_spinor<St, R>(a.in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
+  load_spinor<St, R>(in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
+  load_spinor<St, R>(in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
   if (KIN) {
     const R m = (R)a.mass;
     apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
@@ -259,6 +264,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   constexpr bool DAG = (PASS == PASS_C || PASS == PASS_D);
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = gtid < a.n5;
+  const size_t roff = (size_t)blockIdx.y * a.fstride;  // right-hand side offset (granules)
+  const int rhs = blockIdx.y;
   const int s = threadIdx.x & (a.Ls - 1);
   const size_t x4 = active ? (gtid >> a.lslog2) : 0;
   const size_t site5 = x4 * a.Ls + s;
@@ -268,6 +275,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = 0;
 
+  const uint4* in = a.in + roff;
   // all eight neighbour indices at once (32 bytes, shared by the Ls lanes of a site)
   const int4 nb0 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2);
   const int4 nb1 = __ldg(reinterpret_cast<const int4*>(a.nbr) + x4 * 2 + 1);
@@ -275,10 +283,10 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   const uint4* lk = reinterpret_cast<const uint4*>(a.links) + x4 * 8 * LinkGran<LT>::g;
   // Dh: forward (1 - g), backward (1 + g); Dh^dag flips both.
   constexpr int SF = DAG ? -1 : 1;
-  hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+  hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
 
   double nrm2 = 0.0;
   if (PASS == PASS_A) {
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
       }
     }
     R self[24];
-    load_spinor<St, R>(a.in2, site5, a.n5, self);
+    load_spinor<St, R>(a.in2 + roff, site5, a.n5, self);
     apply_lin<R, DAG>(self, (R)a.alpha, (R)a.beta, s, a.Ls, m);
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = self[i] - R(0.25) * acc[i];
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
       for (int i = 0; i < 24; ++i) acc[i] *= sD;
       if (a.extra) {
         R ex[24];
-        load_spinor<St, R>(a.extra, site5, a.n5, ex);
+        load_spinor<St, R>(a.extra + roff, site5, a.n5, ex);
         const R lam = (R)a.lam;
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] += lam * ex[i];
@@ -327,25 +335,26 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
     }
   }
   if (PASS == PASS_D && a.cg_r) {
-    double den = *a.al_den0;
-    if (a.al_den1) den += a.al_lam * (*a.al_den1);
-    const R alpha = (R)(den != 0.0 ? *a.al_num / den : 0.0);
+    double den = a.al_den0[rhs];
+    if (a.al_den1) den += a.al_lam * a.al_den1[rhs];
+    const bool live = a.al_mask == nullptr || a.al_mask[rhs] != 0;
+    const R alpha = (R)((den != 0.0 && live) ? a.al_num[rhs] / den : 0.0);
     if (active) {
       R rv[24], xv[24], pv[24];
-      load_spinor<St, R>(a.cg_r, site5, a.n5, rv);
-      load_spinor<St, R>(a.cg_x, site5, a.n5, xv);
-      load_spinor<St, R>(a.cg_p, site5, a.n5, pv);
+      load_spinor<St, R>(a.cg_r + roff, site5, a.n5, rv);
+      load_spinor<St, R>(a.cg_x + roff, site5, a.n5, xv);
+      load_spinor<St, R>(a.cg_p + roff, site5, a.n5, pv);
 #pragma unroll
       for (int i = 0; i < 24; ++i) {
         rv[i] -= alpha * acc[i];
         xv[i] += alpha * pv[i];
         acc[i] = rv[i];
       }
-      store_spinor<St, R>(a.cg_r, site5, a.n5, rv);
-      store_spinor<St, R>(a.cg_x, site5, a.n5, xv);
+      store_spinor<St, R>(a.cg_r + roff, site5, a.n5, rv);
+      store_spinor<St, R>(a.cg_x + roff, site5, a.n5, xv);
     }
   } else if (active) {
-    store_spinor<St, R>(a.out, site5, a.n5, acc);
+    store_spinor<St, R>(a.out + roff, site5, a.n5, acc);
   }
   if (a.do_red) {
     if (active) {
@@ -364,7 +373,7 @@ constexpr int HOP_VARIANTS = 3;  // MINB = 1, 2, 3
 
 // launch variant v (0..2) of one pass for storage St
 template <typename St>
-void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st) {
+void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st) {
 #define HDCG_HOP_CASE(P, M)                                                      \
   if (pass == P && v == M - 1) {                                                 \
     if (mob) hop_kernel<St, P, true, M><<<grid, 256, 0, st>>>(a);               \
@@ -379,10 +388,10 @@ void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, unsigned gr
 }
 
 // explicit instantiations live in dwf_<prec>.cu
-void launch_hop_f64(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
-void launch_hop_f32(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
-void launch_hop_f16(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
-void launch_hop_bf16(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
-void launch_hop_bf16t(int v, int pass, bool mob, const HopArgs& a, unsigned grid, cudaStream_t st);
+void launch_hop_f64(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
+void launch_hop_f32(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
+void launch_hop_f16(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
+void launch_hop_bf16(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
+void launch_hop_bf16t(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
 
 }  // namespace hdcg

@@ -37,10 +37,12 @@ enum {
   D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27
 };
 
-static double* dsc(Ctx& c, int slot) { return c.scalars.as<double>() + slot; }
+static double* dsc(Ctx& c, int slot) { return c.scalars.as<double>() + slot * RMAX; }
 
+// read scalar slots [slot, slot + n) of right-hand side 0
 static void read_scalars(Ctx& c, int slot, int n, double* h) {
-  HDCG_CUDA(cudaMemcpyAsync(h, dsc(c, slot), n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  for (int i = 0; i < n; ++i)
+    HDCG_CUDA(cudaMemcpyAsync(h + i, dsc(c, slot + i), sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
 
@@ -57,15 +59,24 @@ static void copy_field(Ctx& c, int prec, const uint4* in, uint4* out) {
 // niter_fixed > 0: exactly that many iterations (M_IRS); otherwise iterate to
 // |r| <= tol |b| (checked on the host every iteration).
 // ---------------------------------------------------------------------------
+static void copy_fields(Ctx& c, int prec, const uint4* in, uint4* out, int R) {
+  HDCG_CUDA(cudaMemcpyAsync(out, in, c.field_bytes(prec) * R, cudaMemcpyDeviceToDevice, c.stream));
+}
+
+static void copy_scalars(Ctx& c, int dst, int src, int R) {
+  HDCG_CUDA(cudaMemcpyAsync(dsc(c, dst), dsc(c, src), R * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+}
+
 static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, int niter_fixed, double tol,
-                      int maxiter, int* n_mdagm) {
-  uint4* res = c.scratch(prec, SL_MRES);
-  uint4* p = c.scratch(prec, SL_MP);
-  zero_field(c, x, prec);
-  copy_field(c, prec, b, res);
-  copy_field(c, prec, b, p);
-  norm2(c, b, prec, 0, dsc(c, D_MRR));
-  copy_scalar(c, D_MPP, D_MRR);
+                      int maxiter, int* n_mdagm, int R = 1) {
+  HDCG_REQUIRE(R == 1 || niter_fixed > 0, HDCG_ERR_ARG, "several right-hand sides need a fixed iteration count");
+  uint4* res = c.scratch(prec, SL_MRES, R);
+  uint4* p = c.scratch(prec, SL_MP, R);
+  zero_field(c, x, prec, R);
+  copy_fields(c, prec, b, res, R);
+  copy_fields(c, prec, b, p, R);
+  norm2(c, b, prec, 0, dsc(c, D_MRR), R);
+  copy_scalars(c, D_MPP, D_MRR, R);
   double bb = 0.0;
   if (niter_fixed <= 0) {
     read_scalars(c, D_MRR, 1, &bb);
@@ -76,8 +87,8 @@ static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, 
   for (; it < nit; ++it) {
     const int par = it & 1;
     apply_mdagm_cg(c, prec, p, shift, x, res, dsc(c, D_MRR + par), dsc(c, D_MPW), dsc(c, D_MPP),
-                   dsc(c, D_MRR + (par ^ 1)));
-    if (n_mdagm) ++*n_mdagm;
+                   dsc(c, D_MRR + (par ^ 1)), R);
+    if (n_mdagm) *n_mdagm += R;
     if (niter_fixed <= 0) {
       double rr = 0.0;
       read_scalars(c, D_MRR + (par ^ 1), 1, &rr);
@@ -92,7 +103,7 @@ static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, 
     ScalarRef be;
     be.num = dsc(c, D_MRR + (par ^ 1));
     be.den0 = dsc(c, D_MRR + par);
-    update_p(c, prec, p, res, be, dsc(c, D_MPP));
+    update_p(c, prec, p, res, be, dsc(c, D_MPP), R);
   }
   return niter_fixed > 0 ? nit : it;
 }
@@ -100,7 +111,8 @@ static int cg_shifted(Ctx& c, int prec, const uint4* b, uint4* x, double shift, 
 // ---------------------------------------------------------------------------
 // Q t = P A^-1 R t (+ add) in the sloppy precision
 // ---------------------------------------------------------------------------
-static void apply_Q(Ctx& c, int sp, const uint4* t, uint4* out, const uint4* add, const hdcg_params& prm,
+// out (precision oprec) = add (oprec) + P A^-1 R t, t in precision sp
+static void apply_Q(Ctx& c, int sp, const uint4* t, uint4* out, int oprec, const uint4* add, const hdcg_params& prm,
                     hdcg_stats* st) {
   Subspace& s = *c.sub;
   Coarse& A = *c.coarse;
@@ -124,7 +136,7 @@ static void apply_Q(Ctx& c, int sp, const uint4* t, uint4* out, const uint4* add
     if (it > st->coarse_iterations_max) st->coarse_iterations_max = it;
   }
   PhaseTimer pt(c, PH_TRANSFER);
-  prolong_field(c, s, cout, cp, out, sp, add);
+  prolong_field(c, s, cout, cp, out, oprec, add);
 }
 
 // y = M1 r in precision op (A-DEF2) ; r in op.  M1 is linear (M_IRS runs a
@@ -155,12 +167,19 @@ static void apply_M1(Ctx& c, int op, int sp, const uint4* r, uint4* y, const hdc
   }
   if (st) st->n_mdagm_sloppy += nm;
   if (sp == op) {
-    apply_Q(c, sp, t, y, z, prm, st);
+    apply_Q(c, sp, t, y, sp, z, prm, st);
+  } else if (scaled) {
+    // the coarse-grid correction amplifies low modes by up to 1 / lambda_min(H),
+    // beyond the FP16 range: z + Q t is formed and kept in FP32
+    uint4* zf = c.scratch(HDCG_F32, SL_Z);
+    uint4* yf = c.scratch(HDCG_F32, SL_MRES);
+    convert_field(c, z, sp, zf, HDCG_F32);
+    apply_Q(c, sp, t, yf, HDCG_F32, zf, prm, st);
+    convert_scaled(c, yf, HDCG_F32, y, op, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
   } else {
     uint4* ys = c.scratch(sp, SL_MRES);
-    apply_Q(c, sp, t, ys, z, prm, st);
-    if (scaled) convert_scaled(c, ys, sp, y, op, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
-    else convert_field(c, ys, sp, y, op);
+    apply_Q(c, sp, t, ys, sp, z, prm, st);
+    convert_field(c, ys, sp, y, op);
   }
 }
 
@@ -174,10 +193,15 @@ static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdc
   } else {
     convert_field(c, b64, HDCG_F64, bs, sp);
   }
-  uint4* x0 = c.scratch(sp, SL_T);
-  apply_Q(c, sp, bs, x0, nullptr, prm, st);
-  if (scaled) convert_scaled(c, x0, sp, xhi, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
-  else convert_field(c, x0, sp, xhi, HDCG_F64);
+  if (scaled) {
+    uint4* x0 = c.scratch(HDCG_F32, SL_T);
+    apply_Q(c, sp, bs, x0, HDCG_F32, nullptr, prm, st);
+    convert_scaled(c, x0, HDCG_F32, xhi, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), 1);
+  } else {
+    uint4* x0 = c.scratch(sp, SL_T);
+    apply_Q(c, sp, bs, x0, sp, nullptr, prm, st);
+    convert_field(c, x0, sp, xhi, HDCG_F64);
+  }
 }
 
 // r64 = b - H64 x_hi; returns |r64|^2 (host), r (op) = r64
@@ -274,7 +298,7 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
       ScalarRef be;
       be.num = dsc(c, D_RYN);
       be.den0 = dsc(c, D_RY);
-      be.den1 = prm.flexible ? dsc(c, D_RYN + 1) : nullptr;
+      be.den1 = prm.flexible ? dsc(c, D_RYN) + 1 : nullptr;  // (r, y_old): second value of the pair
       update_p(c, op, p, yn, be, nullptr);
       copy_scalar(c, D_RY, D_RYN);
       std::swap(y, yn);
@@ -292,6 +316,227 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
   return status;
 }
 
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides in lockstep (the batched driver).  Every kernel
+// covers all R right-hand sides (grid y or a trailing right-hand-side index);
+// alpha and beta are per right-hand side; a device mask freezes right-hand
+// sides whose true residual has converged.  The coarse level reads the
+// subspace and the little Dirac operator once per step for all of them.
+// ---------------------------------------------------------------------------
+static void apply_Q_multi(Ctx& c, int sp, int R, const uint4* t, uint4* out, int oprec, const uint4* add,
+                          const hdcg_params& prm, hdcg_stats* st) {
+  Subspace& s = *c.sub;
+  Coarse& A = *c.coarse;
+  const int cp = A.vec_prec();
+  const size_t nc = A.Vc * A.nvec * (size_t)R;
+  A.qvec.ensure(2 * nc * 16);
+  char* q0 = A.qvec.as<char>();
+  void* cin = q0;
+  void* cout = q0 + nc * 16;
+  {
+    PhaseTimer pt(c, PH_TRANSFER);
+    restrict_multi(c, s, t, sp, R, cin, cp);
+  }
+  int it = 0;
+  {
+    PhaseTimer pt(c, PH_COARSE);
+    it = coarse_cg_multi(c, A, R, cin, cout, prm.coarse_tol, prm.coarse_maxiter);
+  }
+  if (st) {
+    st->coarse_iterations += it;
+    if (it > st->coarse_iterations_max) st->coarse_iterations_max = it;
+  }
+  PhaseTimer pt(c, PH_TRANSFER);
+  prolong_multi(c, s, cout, cp, R, out, oprec, add);
+}
+
+static void apply_M1_multi(Ctx& c, int op, int sp, int R, const uint4* r, uint4* y, const hdcg_params& prm,
+                           hdcg_stats* st) {
+  const uint4* rs = r;
+  const bool scaled = is_16bit(sp);
+  if (scaled) {
+    norm2(c, r, op, 0, dsc(c, D_TMP), R);
+    uint4* t = c.scratch(sp, SL_RS, R);
+    convert_scaled(c, r, op, t, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0, R);
+    rs = t;
+  } else if (sp != op) {
+    uint4* t = c.scratch(sp, SL_RS, R);
+    convert_field(c, r, op, t, sp, R);
+    rs = t;
+  }
+  uint4* z = c.scratch(sp, SL_Z, R);
+  uint4* t = c.scratch(sp, SL_T, R);
+  int nm = 0;
+  {
+    PhaseTimer pt(c, PH_H_SLOPPY);
+    cg_shifted(c, sp, rs, z, prm.mirs_shift, prm.mirs_iter, 0.0, prm.mirs_iter, &nm, R);
+    apply_mdagm_multi(c, sp, R, z, t, nullptr, -1.0, 1.0, rs);  // t = r - H z
+    nm += R;
+  }
+  if (st) st->n_mdagm_sloppy += nm;
+  if (sp == op) {
+    apply_Q_multi(c, sp, R, t, y, sp, z, prm, st);
+  } else if (scaled) {
+    uint4* zf = c.scratch(HDCG_F32, SL_Z, R);
+    uint4* yf = c.scratch(HDCG_F32, SL_MRES, R);
+    convert_field(c, z, sp, zf, HDCG_F32, R);
+    apply_Q_multi(c, sp, R, t, yf, HDCG_F32, zf, prm, st);
+    convert_scaled(c, yf, HDCG_F32, y, op, dsc(c, D_NREAL), dsc(c, D_TMP), 1, R);
+  } else {
+    uint4* ys = c.scratch(sp, SL_MRES, R);
+    apply_Q_multi(c, sp, R, t, ys, sp, z, prm, st);
+    convert_field(c, ys, sp, y, op, R);
+  }
+}
+
+static void start_vector_multi(Ctx& c, int sp, int R, const uint4* b64, uint4* xhi, const hdcg_params& prm,
+                               hdcg_stats* st) {
+  uint4* bs = c.scratch(sp, SL_RS, R);
+  const bool scaled = is_16bit(sp);
+  if (scaled) {
+    norm2(c, b64, HDCG_F64, 0, dsc(c, D_TMP), R);
+    convert_scaled(c, b64, HDCG_F64, bs, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0, R);
+    uint4* x0 = c.scratch(HDCG_F32, SL_T, R);
+    apply_Q_multi(c, sp, R, bs, x0, HDCG_F32, nullptr, prm, st);
+    convert_scaled(c, x0, HDCG_F32, xhi, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), 1, R);
+  } else {
+    convert_field(c, b64, HDCG_F64, bs, sp, R);
+    uint4* x0 = c.scratch(sp, SL_T, R);
+    apply_Q_multi(c, sp, R, bs, x0, sp, nullptr, prm, st);
+    convert_field(c, x0, sp, xhi, HDCG_F64, R);
+  }
+}
+
+// r64_k = b_k - H64 x_k for all right-hand sides; rr[k] on the host; r (op) = r64
+static void true_residual_multi(Ctx& c, int op, int R, const uint4* b64, const uint4* xhi, uint4* r, double* rr,
+                                hdcg_stats* st) {
+  uint4* r64 = c.scratch(HDCG_F64, SL_R64, R);
+  {
+    PhaseTimer pt(c, PH_H_F64);
+    apply_mdagm_multi(c, HDCG_F64, R, xhi, r64, nullptr, -1.0, 1.0, b64);
+  }
+  if (st) st->n_mdagm_f64 += R;
+  norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR), R);
+  if (op != HDCG_F64) convert_field(c, r64, HDCG_F64, r, op, R);
+  else copy_fields(c, HDCG_F64, r64, r, R);
+  HDCG_CUDA(cudaMemcpyAsync(rr, dsc(c, D_RR), R * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+static int solve_batch(Ctx& c, const uint4* b64, uint4* x64, int R, double tol, const hdcg_params& prm,
+                       hdcg_stats* st) {
+  const int op = prm.outer_prec, sp = prm.sloppy_prec;
+  const bool adef2 = prm.algorithm == HDCG_ALG_ADEF2;
+  HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides per batch");
+  HDCG_REQUIRE(op == HDCG_F64 || op == HDCG_F32, HDCG_ERR_ARG, "outer precision must be F64 or F32");
+  if (adef2) HDCG_REQUIRE(c.sub && c.coarse, HDCG_ERR_STATE, "A-DEF2 needs a subspace and a coarse operator");
+  uint4* xlo = c.scratch(op, SL_XLO, R);
+  uint4* r = c.scratch(op, SL_R, R);
+  uint4* p = c.scratch(op, SL_P, R);
+  uint4* y = c.scratch(op, SL_Y, R);
+  uint4* yn = c.scratch(op, SL_YN, R);
+  uint4* xhi = x64;
+  DevMem dmask;
+  dmask.ensure(RMAX * sizeof(int));
+  int mask[RMAX] = {0};
+  auto upload_mask = [&]() {
+    HDCG_CUDA(cudaMemcpyAsync(dmask.p, mask, RMAX * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  };
+  double bb[RMAX], rr[RMAX], rr_rel[RMAX], stop[RMAX];
+  norm2(c, b64, HDCG_F64, 0, dsc(c, D_BB), R);
+  HDCG_CUDA(cudaMemcpyAsync(bb, dsc(c, D_BB), R * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  zero_field(c, xhi, HDCG_F64, R);
+  zero_field(c, xlo, op, R);
+  if (adef2) start_vector_multi(c, sp, R, b64, xhi, prm, st);
+  true_residual_multi(c, op, R, b64, xhi, r, rr, st);
+  int nactive = 0;
+  for (int k = 0; k < R; ++k) {
+    stop[k] = tol * tol * bb[k];
+    rr_rel[k] = rr[k];
+    mask[k] = (bb[k] > 0.0 && rr[k] > stop[k]) ? 1 : 0;
+    nactive += mask[k];
+  }
+  upload_mask();
+  int it = 0;
+  int status = nactive ? HDCG_NOT_CONVERGED : HDCG_OK;
+  if (nactive) {
+    if (adef2) {
+      apply_M1_multi(c, op, sp, R, r, y, prm, st);
+      copy_fields(c, op, y, p, R);
+      redot2(c, op, r, y, nullptr, dsc(c, D_RYN), R);
+      HDCG_CUDA(cudaMemcpy2DAsync(dsc(c, D_RY), sizeof(double), dsc(c, D_RYN), 2 * sizeof(double), sizeof(double), R,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+      copy_fields(c, op, r, p, R);
+      copy_scalars(c, D_RY, D_RR, R);
+    }
+  }
+  while (nactive && it < prm.maxiter) {
+    {
+      PhaseTimer pt(c, PH_H_OUTER);
+      apply_mdagm_cg(c, op, p, 0.0, xlo, r, dsc(c, D_RY), dsc(c, D_PW), nullptr, dsc(c, D_RR), R,
+                     dmask.as<int>());
+    }
+    st->n_mdagm_outer += R;
+    ++it;
+    double pw[RMAX];
+    HDCG_CUDA(cudaMemcpyAsync(pw, dsc(c, D_PW), R * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    HDCG_CUDA(cudaMemcpyAsync(rr, dsc(c, D_RR), R * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    HDCG_CUDA(cudaStreamSynchronize(c.stream));
+    bool need = it >= prm.maxiter;
+    for (int k = 0; k < R; ++k) {
+      if (!mask[k]) continue;
+      HDCG_REQUIRE(std::isfinite(pw[k]) && std::isfinite(rr[k]), HDCG_ERR_NONFINITE, "non-finite residual");
+      HDCG_REQUIRE(pw[k] > 0.0, HDCG_ERR_BREAKDOWN, "(p, Hp) <= 0");
+      if (rr[k] <= prm.reliable_delta * prm.reliable_delta * rr_rel[k] || rr[k] <= stop[k]) need = true;
+    }
+    if (need) {
+      accum_hi(c, HDCG_F64, xhi, op, xlo, R);
+      true_residual_multi(c, op, R, b64, xhi, r, rr, st);
+      ++st->reliable_updates;
+      nactive = 0;
+      for (int k = 0; k < R; ++k) {
+        if (!mask[k]) continue;
+        rr_rel[k] = rr[k];
+        if (rr[k] <= stop[k]) mask[k] = 0;
+        nactive += mask[k];
+      }
+      upload_mask();
+      if (!nactive) {
+        status = HDCG_OK;
+        break;
+      }
+    }
+    if (adef2) {
+      apply_M1_multi(c, op, sp, R, r, yn, prm, st);
+      redot2(c, op, r, yn, y, dsc(c, D_RYN), R);
+      ScalarRef be;
+      be.num = dsc(c, D_RYN);
+      be.den0 = dsc(c, D_RY);
+      be.den1 = prm.flexible ? dsc(c, D_RYN) + 1 : nullptr;
+      be.stride = 2;
+      update_p(c, op, p, yn, be, nullptr, R);
+      HDCG_CUDA(cudaMemcpy2DAsync(dsc(c, D_RY), sizeof(double), dsc(c, D_RYN), 2 * sizeof(double), sizeof(double), R,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+      std::swap(y, yn);
+    } else {
+      ScalarRef be;
+      be.num = dsc(c, D_RR);
+      be.den0 = dsc(c, D_RY);
+      update_p(c, op, p, r, be, nullptr, R);
+      copy_scalars(c, D_RY, D_RR, R);
+    }
+  }
+  st->iterations += it;
+  double worst = 0.0;
+  for (int k = 0; k < R; ++k)
+    if (bb[k] > 0.0) worst = std::max(worst, std::sqrt(rr_rel[k] / bb[k]));
+  if (worst > st->true_residual) st->true_residual = worst;
+  return status;
+}
+
 int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_params& prm, hdcg_stats* st,
           bool on_device) {
   HDCG_REQUIRE(nrhs >= 1, HDCG_ERR_ARG, "nrhs >= 1");
@@ -300,32 +545,37 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
   const auto t0 = std::chrono::steady_clock::now();
   std::memset(st, 0, sizeof(*st));
   const size_t canon = c.n5 * 12 * sizeof(double2);
-  DevMem hb;
-  uint4* b64 = c.scratch(HDCG_F64, SL_B);
-  uint4* x64 = c.scratch(HDCG_F64, SL_XHI);
   int worst = HDCG_OK;
-  for (int k = 0; k < nrhs; ++k) {
-    const char* bk = reinterpret_cast<const char*>(b) + k * canon;
-    char* xk = reinterpret_cast<char*>(x) + k * canon;
+  {
+    const double nreal = (double)c.n5 * 24.0;
+    HDCG_CUDA(cudaMemcpyAsync(dsc(c, D_NREAL), &nreal, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  }
+  const int chunk = prm.batch ? RMAX : 1;
+  for (int k0 = 0; k0 < nrhs; k0 += chunk) {
+    const int R = std::min(chunk, nrhs - k0);
+    const char* bk = reinterpret_cast<const char*>(b) + k0 * canon;
+    char* xk = reinterpret_cast<char*>(x) + k0 * canon;
+    uint4* b64 = c.scratch(HDCG_F64, SL_B, R);
+    uint4* x64 = c.scratch(HDCG_F64, SL_XHI, R);
     if (on_device) {
-      canon_to_internal(c, bk, HDCG_F64, b64, HDCG_F64);
+      canon_to_internal(c, bk, HDCG_F64, b64, HDCG_F64, R);
     } else {
-      c.canon_in.ensure(canon);
-      HDCG_CUDA(cudaMemcpyAsync(c.canon_in.p, bk, canon, cudaMemcpyHostToDevice, c.stream));
-      canon_to_internal(c, c.canon_in.p, HDCG_F64, b64, HDCG_F64);
+      c.canon_in.ensure(canon * R);
+      HDCG_CUDA(cudaMemcpyAsync(c.canon_in.p, bk, canon * R, cudaMemcpyHostToDevice, c.stream));
+      canon_to_internal(c, c.canon_in.p, HDCG_F64, b64, HDCG_F64, R);
     }
     int rc;
     {
       PhaseTimer pt(c, PH_TOTAL);
-      rc = solve_one(c, b64, x64, tol, prm, st);
+      rc = R == 1 ? solve_one(c, b64, x64, tol, prm, st) : solve_batch(c, b64, x64, R, tol, prm, st);
     }
     if (rc != HDCG_OK) worst = rc;
     if (on_device) {
-      internal_to_canon(c, x64, HDCG_F64, xk, HDCG_F64);
+      internal_to_canon(c, x64, HDCG_F64, xk, HDCG_F64, R);
     } else {
-      c.canon_out.ensure(canon);
-      internal_to_canon(c, x64, HDCG_F64, c.canon_out.p, HDCG_F64);
-      HDCG_CUDA(cudaMemcpyAsync(xk, c.canon_out.p, canon, cudaMemcpyDeviceToHost, c.stream));
+      c.canon_out.ensure(canon * R);
+      internal_to_canon(c, x64, HDCG_F64, c.canon_out.p, HDCG_F64, R);
+      HDCG_CUDA(cudaMemcpyAsync(xk, c.canon_out.p, canon * R, cudaMemcpyDeviceToHost, c.stream));
     }
   }
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
@@ -343,7 +593,11 @@ void build_subspace(Ctx& c, const hdcg_subspace_params& p) {
     HDCG_REQUIRE(p.block[mu] >= 4, HDCG_ERR_ARG, "block extents must be >= 4 (Sec. 5.1)");
   if (!c.sub) c.sub = new Subspace();
   Subspace& s = *c.sub;
-  subspace_init(c, s, p.block, p.nvec, p.prec);
+  // a 16-bit subspace is built in FP32 and rounded once at the end: inverse
+  // iteration makes the block pieces nearly dependent, which 16-bit storage
+  // would blur before the block orthonormalisation can separate them
+  const bool round_at_end = p.prec == HDCG_F16;
+  subspace_init(c, s, p.block, p.nvec, round_at_end ? HDCG_F32 : p.prec);
   subspace_noise(c, s, p.seed);
   const int wp = p.prec == HDCG_F64 ? HDCG_F64 : HDCG_F32;
   uint4* bk = c.scratch(wp, SL_CGB);
@@ -357,6 +611,15 @@ void build_subspace(Ctx& c, const hdcg_subspace_params& p) {
     block_orthonormalise(c, s);
   }
   if (p.inv_steps <= 0) block_orthonormalise(c, s);
+  if (round_at_end) {
+    DevMem v32;
+    std::swap(v32.p, s.vecs.p);
+    std::swap(v32.bytes, s.vecs.bytes);
+    s.prec = HDCG_F16;
+    s.vecs.ensure((size_t)s.nvec * s.vec_bytes(c));
+    convert_field(c, v32.as<uint4>(), HDCG_F32, s.vecs.as<uint4>(), HDCG_F16, s.nvec);
+    block_orthonormalise(c, s);
+  }
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
 

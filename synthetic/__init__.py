@@ -147,3 +147,19 @@ def gaussian_fermions(dims, Ls: int, seed: int, count: int) -> np.ndarray:
 def coarse_gaussian(n_sites: int, nvec: int, seed: int) -> np.ndarray:
     """Gaussian coarse vector, canonical (n_sites, nvec) complex128."""
     return complex_normal(seed, (n_sites, nvec))
+
+
+def point_sources(dims, Ls, count: int = 12) -> np.ndarray:
+    """Spin-colour point sources on the odd-checkerboard system, one per
+    (spin, colour) pair, at the odd site x = (1, 0, 0, 0): chirality-plus spins
+    (0, 1) on the wall s = 0, chirality-minus spins (2, 3) on the wall s = Ls - 1.
+    Shape (count, V/2, Ls, 4, 3); count <= 12 takes the first pairs."""
+    check_dims(dims)
+    v2 = volume(dims) // 2
+    out = np.zeros((count, v2, Ls, 4, 3), dtype=np.complex128)
+    cb = 1 >> 1                      # lex index 1 (x = 1) is odd; cb = lex >> 1
+    for k in range(count):
+        spin, colour = (k // 3) % 4, k % 3
+        s = 0 if spin < 2 else Ls - 1
+        out[k, cb, s, spin, colour] = 1.0
+    return out

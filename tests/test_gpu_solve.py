@@ -128,3 +128,65 @@ def test_two_level_workload_8x8x8x8_ls8_fp64():
     assert _true_res(d, b, c) <= 1.05 * w.tol
     assert rel(a, c) < 1e-6
     assert s1.iterations < s2.iterations
+
+
+def _sources(d, n, seed):
+    """n right-hand sides of uneven difficulty: Gaussian ones and point sources."""
+    out = []
+    for k in range(n):
+        if k % 3 == 2:
+            b = np.zeros(d.field_shape, dtype=np.complex128)
+            b[(7 * k) % d.field_shape[0], 0, k % 4, k % 3] = 1.0
+            b[(7 * k) % d.field_shape[0], d.Ls - 1, (k + 2) % 4, k % 3] = 1.0
+        else:
+            b = sy.gaussian_fermion(d.lat.dims, d.Ls, seed + k)
+        out.append(b)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("alg,outer,sloppy,nrhs", [
+    (ALG_ADEF2, F32, F32, 4),
+    (ALG_ADEF2, F32, F16, 5),
+    (ALG_CG, F32, F32, 3),
+    (ALG_ADEF2, F64, F64, 2),
+])
+def test_batched_solve(small, alg, outer, sloppy, nrhs):
+    """Lockstep solve of several right-hand sides with uneven convergence: each
+    solution meets its true residual (oracle) and agrees with the oracle's CG."""
+    torch, d, bl, phi, b0, xs0 = small
+    h = _handle(d, torch)
+    if alg == ALG_ADEF2:
+        h.set_subspace((4, 4, 4, 4), torch.from_numpy(phi).cuda(), prec=F64 if outer == F64 else F32,
+                       already_orthonormal=True)
+        h.build_coarse(F64 if outer == F64 else F32)
+    tol = 1e-10 if outer == F64 else 1e-8
+    B = _sources(d, nrhs, 820)
+    bt = torch.from_numpy(B).cuda()
+    x = torch.zeros_like(bt)
+    st = h.solve(bt, x, tol, Hdcg.default_params(algorithm=alg, outer_prec=outer, sloppy_prec=sloppy,
+                                                  maxiter=20000), nrhs=nrhs)
+    assert st.status == 0
+    X = x.cpu().numpy()
+    for k in range(nrhs):
+        assert _true_res(d, B[k], X[k]) <= 1.05 * tol, f"rhs {k}"
+        xk, _ = cg(d.mdagm, B[k], 1e-12)
+        assert rel(X[k], xk) < 1e-5, f"rhs {k}"
+
+
+def test_batched_equals_sequential_and_chunks(small):
+    """batch=1 and batch=0 reach the same solutions; 17 right-hand sides run as
+    a batch of 16 plus one."""
+    torch, d, bl, phi, b0, xs0 = small
+    h = _handle(d, torch)
+    h.set_subspace((4, 4, 4, 4), torch.from_numpy(phi).cuda(), prec=F32, already_orthonormal=True)
+    h.build_coarse(F32)
+    B = _sources(d, 17, 840)
+    bt = torch.from_numpy(B).cuda()
+    xb, xq = torch.zeros_like(bt), torch.zeros_like(bt)
+    sb = h.solve(bt, xb, 1e-8, Hdcg.default_params(batch=1), nrhs=17)
+    sq = h.solve(bt, xq, 1e-8, Hdcg.default_params(batch=0), nrhs=17)
+    assert sb.status == 0 and sq.status == 0
+    Xb, Xq = xb.cpu().numpy(), xq.cpu().numpy()
+    for k in range(17):
+        assert _true_res(d, B[k], Xb[k]) <= 1.05e-8
+        assert rel(Xb[k], Xq[k]) < 1e-5
