@@ -228,6 +228,12 @@ def run_ours(args, w):
         stats.append(st.as_dict())
     launches = h.launch_count() - launches0
     n_hop, hop_ms, hop_bytes = h.get_hop_profile(outer)
+    hop_all = {}
+    for pname, pc in (("f64", 0), ("f32", 1), ("f16", 2), ("bf16", 3)):
+        n_p, ms_p, by_p = h.get_hop_profile(pc)
+        if n_p:
+            hop_all[pname] = {"launches": n_p, "avg_launch_us": ms_p * 1e3 / n_p,
+                              "GBps": by_p / (ms_p / 1e3) / 1e9 if ms_p > 0 else None}
     phases = {k: v / args.steps for k, v in h.get_phase_profile().items()}
     h.set_profiling(False)
     clocks = clk.stop()
@@ -319,6 +325,7 @@ def run_ours(args, w):
                  "n_mdagm_f64": s0["n_mdagm_f64"], "reliable_updates": s0["reliable_updates"],
                  "true_residual": s0["true_residual"]},
         "phases_ms_per_solve": phases,
+        "hop_profile": hop_all,
         "sequential_single_rhs": seq,
         "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse,
                           "inverse_iteration": {"steps": args.inv_steps, "tol": args.inv_tol}},
@@ -375,7 +382,7 @@ def run_coarse_only(args, w):
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(sy.gauge_field(w.dims, w.eps, w.gauge_seed)).to(dev))
     h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=0, seed=w.subspace_seed)
-    h.build_coarse(sub_prec if sub_prec != 2 else 2)
+    h.build_coarse(PREC[args.coarse_prec] if args.coarse_prec else sub_prec)
     vc = 1
     for d, b in zip(w.dims, w.block):
         vc *= d // b
@@ -383,12 +390,18 @@ def run_coarse_only(args, w):
     y = torch.empty_like(x)
     h.coarse_apply(x, y)
     torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    e0.record(stream)
     for _ in range(args.coarse_only):
         h.coarse_apply(x, y)
+    e1.record(stream)
     torch.cuda.synchronize(dev)
     print(json.dumps({"workload": w.name, "coarse_applies": args.coarse_only,
-                      "ms_per_call": (time.perf_counter() - t0) * 1e3 / args.coarse_only}), flush=True)
+                      "coarse_storage": args.coarse_prec or w.prec,
+                      "ms_per_call_device": e0.elapsed_time(e1) / args.coarse_only,
+                      "ms_per_call_host": (time.perf_counter() - t0) * 1e3 / args.coarse_only}), flush=True)
 
 
 def main():

@@ -64,6 +64,8 @@ extern "C" {
 #define HDCG_ERR_CUDA      -3  /* a CUDA call failed */
 #define HDCG_ERR_NONFINITE -4  /* a residual or inner product became NaN/Inf */
 #define HDCG_ERR_BREAKDOWN -5  /* (p, Hp) <= 0 or (r, y) <= 0 in a Krylov step */
+#define HDCG_ERR_TIMEOUT   -6  /* a bounded device-side wait expired (tensor-core pipeline); the
+                                 context stays usable, the result of that call is undefined */
 #define HDCG_ERR_STATE     -7  /* prerequisite missing (no gauge field, no subspace, ...) */
 
 /* solver algorithms */
@@ -132,8 +134,23 @@ int hdcg_get_subspace(hdcg_t h, void* phi_host);
  * precision of A (HDCG_F64, _F32 or _F16).  Synchronous. */
 int hdcg_build_coarse(hdcg_t h, int prec);
 
+/* Canonical layout of A: complex double [Vc][81][j][k], block (a, l) couples
+ * coarse site a to its neighbour a + delta_l with
+ * l = (dx+1) + 3 (dy+1) + 9 (dz+1) + 27 (dt+1), delta in {-1,0,1}^4, coarse
+ * sites lexicographic in the block coordinates (x fastest); y_a = sum_l
+ * A[a][l] x_{a+delta_l}.  Along a coarse extent of 2 only the offsets 0, +1
+ * are stored (-1 is the same neighbour), along an extent of 1 only 0; the
+ * other blocks are zero.  */
+
 /* Copy A out in the canonical layout (complex double, host).  Synchronous. */
 int hdcg_get_coarse(hdcg_t h, void* A_host);
+
+/* Upload a little Dirac operator in the canonical layout (host or device
+ * pointer, complex double), stored in precision prec (F64, F32 or F16; round
+ * to nearest).  A subspace must be set first: it fixes the blocking, Vc and
+ * Nvec; prec is F64 exactly when the subspace is.  Replaces any operator
+ * built before.  Synchronous. */
+int hdcg_set_coarse(hdcg_t h, const void* A, int prec, int on_device);
 
 /* c = R v (c[b][k] = <phi_k^b, v>), v a canonical odd field of precision prec on
  * the device, c a canonical coarse vector (complex double, device). */
@@ -142,6 +159,14 @@ int hdcg_restrict(hdcg_t h, const void* v, int prec, void* c);
 int hdcg_prolong(hdcg_t h, const void* c, void* v, int prec);
 /* y = A x on canonical coarse vectors (complex double, device). */
 int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
+
+/* Y = A X for nrhs (1..16) coarse vectors at once (Sec. 4.3 stencil, one read of
+ * A for all of them).  x, y: canonical [nrhs][Vc][Nvec] complex double, device.
+ * An FP16 operator runs on the tensor cores (tcgen05, FP32 accumulation; X
+ * enters as a scaled FP16 hi + lo pair per value, about 22 significant bits),
+ * FP32/FP64 operators on the CUDA cores.  HDCG_ERR_TIMEOUT if a device-side
+ * pipeline wait expired.  Synchronous. */
+int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
 
 /* y = A x exactly like hdcg_coarse_apply, but without allocating any device
  * memory: for callers that cannot call cudaMalloc on this path (for example a

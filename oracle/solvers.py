@@ -11,6 +11,22 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                shift and tolerance are readings, not values printed by the paper).
 * ``DeflationSpace``  Q = P A^-1 R (Sec. 2) with the coarse solve by CG to a
                relative residual (Table optimised: 0.04 inside the solver) or exact.
+* ``ldop_deflation_space``  second-level (global, unblocked) deflation vectors
+               of the little Dirac operator (Sec. 5.2, "Little Dirac operator
+               deflation"): steps of shifted inverse iteration on Gaussian start
+               vectors, each followed by a global Gram-Schmidt, then the
+               prediagonalisation (Rayleigh-Ritz on their span) that makes the
+               third, dense level diagonal.
+* ``adef1``    the A-DEF1 method applied to the little Dirac operator with those
+               vectors: V_start = 0, M_1 = M P_L + Q, M_2 = M_3 = 1 (Sec. 5.2,
+               "Truncated little Dirac operator as preconditioner"), with the
+               high-mode preconditioner M = 1 (the Chebyshev polynomial of
+               Q_trunc is not part of this oracle).  Reading: Table algos prints
+               M_2 = P_R in the A-DEF1 row; with V_start = x that keeps every
+               search direction out of span(Z), so the iteration cannot reach
+               the deflated part of the solution (with a complete basis P_R = 0).
+               The generalised algorithm's source (Tang et al., cited with
+               Fig. pcg_general) has M_2 = 1 for A-DEF1, which is taken here.
 * ``adef2``    generalised preconditioned CG of Fig. pcg_general with the
                A-DEF2 row of Table algos: V_start = Q b + P_R x, M_1 = P_R M_IRS + Q,
                M_2 = M_3 = 1.  ``flexible=True`` uses the Polak-Ribiere
@@ -20,7 +36,12 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
 Random numbers drawn by the method (the Gaussian start vectors of the
 subspace) are inputs to these functions.
 
-Parity: cg, mirs, DeflationSpace and adef2 are pinned by
+Parity: ldop_deflation_space and adef1 are pinned by tests/test_oracle_ldop.py
+(Rayleigh-Ritz interlacing and convergence to the exact lowest eigenvalues of
+the dense little Dirac operator, prediagonal third level, A-DEF1 with the
+complete eigenbasis is a direct solve, A-DEF1 reaches the dense solution in
+fewer iterations than CG).
+cg, mirs, DeflationSpace and adef2 are pinned by
 tests/test_oracle_solvers.py (true residual, free-field exact solution,
 A-DEF2 invariants Q r_k = 0 and P_L r_k = r_k with exact Q, QH = 1 - P_R in
 the block form of Sec. 2, deflated and undeflated solutions equal).
@@ -106,6 +127,92 @@ def inverse_iteration_subspace(apply_H, noise, blocking: Blocking, steps: int = 
     return phi
 
 
+def _global_gram_schmidt(Z):
+    """Modified Gram-Schmidt, applied twice, over whole (unblocked) coarse vectors."""
+    Z = np.array(Z, dtype=np.complex128, copy=True)
+    for _ in range(2):
+        for i in range(Z.shape[0]):
+            for j in range(i):
+                Z[i] -= _dot(Z[j], Z[i]) * Z[j]
+            Z[i] /= np.sqrt(_n2(Z[i]))
+    return Z
+
+
+def ldop_deflation_space(A, blocking: Blocking, noise, steps: int = 3, shift: float = 0.0,
+                         tol: float = 1e-7, maxiter: int = 100000):
+    """Global deflation vectors of the little Dirac operator A (Sec. 5.2).
+
+    ``noise`` (nd, Vc, Nvec) are Gaussian start vectors.  Each of ``steps``
+    steps replaces every vector by (A + shift)^-1 of it (CG to ``tol``, the
+    paper's LittleDopSolverResidualSubspace) and then orthonormalises the set;
+    finally the set is prediagonalised: with G = Z^dag A Z = S diag(lam) S^dag,
+    Z <- Z S.  Returns (Z, AZ, lam), lam ascending, so Z^dag A Z = diag(lam).
+    """
+    Aop = lambda v: coarse_apply(A, v, blocking)
+    As = (lambda v: Aop(v) + shift * v) if shift else Aop
+    Z = np.array(noise, dtype=np.complex128, copy=True)
+    for _ in range(steps):
+        for i in range(Z.shape[0]):
+            Z[i], _ = cg(As, Z[i], tol, maxiter)
+        Z = _global_gram_schmidt(Z)
+    nd = Z.shape[0]
+    AZ = np.array([Aop(z) for z in Z])
+    G = Z.reshape(nd, -1).conj() @ AZ.reshape(nd, -1).T
+    G = 0.5 * (G + G.conj().T)
+    lam, S = np.linalg.eigh(G)
+    Zs = np.einsum("ik,i...->k...", S, Z)
+    AZs = np.einsum("ik,i...->k...", S, AZ)
+    return Zs, AZs, lam
+
+
+def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: bool = True,
+          history=None):
+    """A-DEF1 for A x = b with Q = Z diag(lam)^-1 Z^dag, M = 1 (M_2 = 1, see above).
+
+    x_0 = 0, r_0 = b; y = M_1 r = P_L r + Q r = r - A Q r + Q r; p_0 = y_0; then
+    w = A p, alpha = (r, y)/(p, w), x += alpha p, r -= alpha w, y' = M_1 r,
+    beta = (r, y' - y)/(r_old, y_old) (flexible) or (r, y')/(r_old, y_old),
+    p = y' + beta p.  A Q v = (A Z) diag(lam)^-1 Z^dag v uses the stored A Z, so
+    every iteration applies A once.  Returns (x, iterations).
+    """
+    nd = Z.shape[0]
+    Zf = Z.reshape(nd, -1)
+    AZf = AZ.reshape(nd, -1)
+    shape = b.shape
+
+    def M1(r):
+        d = (Zf.conj() @ r.ravel()) / lam
+        return r + ((Zf - AZf).T @ d).reshape(shape)
+
+    x = np.zeros_like(b)
+    r = np.array(b, copy=True)
+    bb = _n2(b)
+    if bb == 0.0:
+        return x, 0
+    y = M1(r)
+    p = y.copy()
+    ry = _dot(r, y).real
+    it = 0
+    while it < maxiter:
+        w = apply_A(p)
+        alpha = ry / _dot(p, w).real
+        x = x + alpha * p
+        r = r - alpha * w
+        it += 1
+        rel = np.sqrt(_n2(r) / bb)
+        if history is not None:
+            history.append(rel)
+        if rel <= tol:
+            break
+        y_new = M1(r)
+        ry_new = _dot(r, y_new).real
+        beta = (ry_new - _dot(r, y).real) / ry if flexible else ry_new / ry
+        p = y_new + beta * p
+        y = y_new
+        ry = ry_new
+    return x, it
+
+
 @dataclass
 class DeflationSpace:
     """Q = sum_{ab} |phi^a> (A^-1)^{ab} <phi^b| (Sec. 2) on an orthonormal block basis."""
@@ -116,6 +223,7 @@ class DeflationSpace:
     coarse_tol: float = 0.0        # 0 -> exact dense solve
     coarse_maxiter: int = 100000
     coarse_iters: list = field(default_factory=list)
+    ldop: tuple = None             # (Z, AZ, lam): coarse solve by A-DEF1 with these vectors
 
     def __post_init__(self):
         self._dense = None
@@ -130,8 +238,11 @@ class DeflationSpace:
     def coarse_solve(self, c):
         if self.coarse_tol == 0.0:
             return np.linalg.solve(self.dense(), c.ravel()).reshape(c.shape)
-        y, it = cg(lambda v: coarse_apply(self.A, v, self.blocking), c,
-                   self.coarse_tol, self.coarse_maxiter)
+        Aop = lambda v: coarse_apply(self.A, v, self.blocking)
+        if self.ldop is not None:
+            y, it = adef1(Aop, c, *self.ldop, self.coarse_tol, self.coarse_maxiter)
+        else:
+            y, it = cg(Aop, c, self.coarse_tol, self.coarse_maxiter)
         self.coarse_iters.append(it)
         return y
 

@@ -16,7 +16,7 @@ F64, F32, F16, BF16, BF16T = 0, 1, 2, 3, 4
 PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "bf16t": BF16T}
 ALG_CG, ALG_ADEF2 = 0, 1
 _ERRORS = {1: "not converged", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
-           -4: "non-finite value", -5: "Krylov breakdown", -7: "missing prerequisite"}
+           -4: "non-finite value", -5: "Krylov breakdown", -6: "device wait timed out", -7: "missing prerequisite"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -70,10 +70,12 @@ _SIGS = {
     "hdcg_get_subspace": (_I, [_P, _P]),
     "hdcg_build_coarse": (_I, [_P, _I]),
     "hdcg_get_coarse": (_I, [_P, _P]),
+    "hdcg_set_coarse": (_I, [_P, _P, _I, _I]),
     "hdcg_restrict": (_I, [_P, _P, _I, _P]),
     "hdcg_prolong": (_I, [_P, _P, _P, _I]),
     "hdcg_coarse_apply": (_I, [_P, _P, _P]),
     "hdcg_coarse_apply_noalloc": (_I, [_P, _P, _P]),
+    "hdcg_coarse_apply_multi": (_I, [_P, _P, _P, _I]),
     "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
     "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
     "hdcg_set_profiling": (_I, [_P, _I]),
@@ -189,6 +191,9 @@ class Hdcg:
     def build_coarse(self, prec=F32):
         return self._check(self._L.hdcg_build_coarse(self.h, prec))
 
+    def set_coarse(self, A, prec=F32):
+        return self._check(self._L.hdcg_set_coarse(self.h, _ptr(A), int(prec), _on_device(A)))
+
     def get_coarse(self, out):
         return self._check(self._L.hdcg_get_coarse(self.h, _ptr(out)))
 
@@ -200,6 +205,9 @@ class Hdcg:
 
     def coarse_apply(self, x, y):
         return self._check(self._L.hdcg_coarse_apply(self.h, _ptr(x), _ptr(y)))
+
+    def coarse_apply_multi(self, x, y, nrhs):
+        return self._check(self._L.hdcg_coarse_apply_multi(self.h, _ptr(x), _ptr(y), int(nrhs)))
 
     def coarse_apply_noalloc(self, x, y):
         return self._check(self._L.hdcg_coarse_apply_noalloc(self.h, _ptr(x), _ptr(y)))

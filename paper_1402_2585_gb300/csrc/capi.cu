@@ -13,6 +13,7 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
           bool on_device);
 void build_subspace(Ctx& c, const hdcg_subspace_params& p);
 void build_coarse(Ctx& c, int prec);
+void set_coarse(Ctx& c, const void* A, int prec, int on_device);
 
 static void resolve_profile(Ctx& c) {
   auto& pr = c.prof;
@@ -230,6 +231,16 @@ int hdcg_build_coarse(hdcg_t h, int prec) {
   return HDCG_OK;
 }
 
+int hdcg_set_coarse(hdcg_t h, const void* A, int prec, int on_device) {
+  HDCG_ENTRY(h, {
+    check_ptr(A, "A");
+    HDCG_REQUIRE(prec == HDCG_F64 || prec == HDCG_F32 || prec == HDCG_F16, HDCG_ERR_ARG,
+                 "coarse precision must be F64, F32 or F16");
+    set_coarse(c, A, prec, on_device);
+  });
+  return HDCG_OK;
+}
+
 int hdcg_get_coarse(hdcg_t h, void* A_host) {
   HDCG_ENTRY(h, {
     check_ptr(A_host, "A");
@@ -292,6 +303,17 @@ int hdcg_coarse_apply(hdcg_t h, const void* x, void* y) {
     coarse_apply(c, *c.coarse, xi, yi, nullptr);
     cvec_convert(c, yi, cp, y, HDCG_F64, nc);
     HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  });
+  return HDCG_OK;
+}
+
+int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs) {
+  HDCG_ENTRY(h, {
+    check_ptr(x, "x");
+    check_ptr(y, "y");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    HDCG_REQUIRE(nrhs >= 1 && nrhs <= RMAX, HDCG_ERR_ARG, "nrhs must be 1..16");
+    coarse_apply_multi_canon(c, *c.coarse, nrhs, x, y);
   });
   return HDCG_OK;
 }

@@ -573,6 +573,8 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   HDCG_REQUIRE(prec == HDCG_F64 || prec == HDCG_F32 || prec == HDCG_F16, HDCG_ERR_ARG,
                "coarse precision must be F64, F32 or F16");
   A.prec = prec;
+  A.tc_ready = false;
+  A.tc_choice = -1;
   A.nvec = s.nvec;
   A.Vc = s.Vc;
   std::vector<int> nb(s.Vc * 81);
@@ -666,6 +668,8 @@ __global__ void k_fourier_solve(const double2* __restrict__ F, const double2* __
 }
 
 void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec) {
+  A.tc_ready = false;
+  A.tc_choice = -1;
   const int n = s.nvec;
   // per-dimension offsets and momenta; compact index q = qx + nx (qy + ny (qz + nz qt))
   std::vector<int> offs[4], moms[4];
@@ -1137,7 +1141,44 @@ static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol
   return h.iter;
 }
 
+// Single right-hand side with an FP16 operator: time eight iterations of the
+// CUDA-core and of the tensor-core coarse CG once per operator, keep the faster.
+static void tune_single(Ctx& c, Coarse& A, const void* rhs, void* sol) {
+  coarse_tc_prepare(c, A);
+  if (c.tuning_off) {
+    A.tc_choice = 1;
+    return;
+  }
+  const int keep = A.last_iters;
+  cudaEvent_t e[3];
+  for (auto& ev : e) HDCG_CUDA(cudaEventCreate(&ev));
+  A.last_iters = 8;
+  coarse_cg_t<__half2, float>(c, A, rhs, sol, 1e-30, 8);
+  coarse_cg_tc(c, A, 1, rhs, sol, 1e-30, 8);
+  HDCG_CUDA(cudaEventRecord(e[0], c.stream));
+  coarse_cg_t<__half2, float>(c, A, rhs, sol, 1e-30, 8);
+  HDCG_CUDA(cudaEventRecord(e[1], c.stream));
+  coarse_cg_tc(c, A, 1, rhs, sol, 1e-30, 8);
+  HDCG_CUDA(cudaEventRecord(e[2], c.stream));
+  HDCG_CUDA(cudaEventSynchronize(e[2]));
+  float t_core = 0, t_tc = 0;
+  HDCG_CUDA(cudaEventElapsedTime(&t_core, e[0], e[1]));
+  HDCG_CUDA(cudaEventElapsedTime(&t_tc, e[1], e[2]));
+  for (auto& ev : e) cudaEventDestroy(ev);
+  A.tc_choice = t_tc < t_core ? 1 : 0;
+  A.last_iters = keep;
+}
+
+bool coarse_use_tc_single(Ctx& c, Coarse& A) {
+  if (!coarse_tc_supported(A)) return false;
+  return A.tc_choice == 1;
+}
+
 int coarse_cg(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter) {
+  if (coarse_tc_supported(A)) {
+    if (A.tc_choice < 0) tune_single(c, A, rhs, sol);
+    if (A.tc_choice == 1) return coarse_cg_tc(c, A, 1, rhs, sol, tol, maxiter);
+  }
   if (A.prec == HDCG_F64) return coarse_cg_t<double2, double>(c, A, rhs, sol, tol, maxiter);
   if (A.prec == HDCG_F32) return coarse_cg_t<float2, float>(c, A, rhs, sol, tol, maxiter);
   return coarse_cg_t<__half2, float>(c, A, rhs, sol, tol, maxiter);
@@ -1178,6 +1219,42 @@ __global__ void k_coarse_export(const AT* A, double2* out, int n, size_t Vc) {
     const float2 v = __half22float2(((const __half2*)A)[src]);
     out[t] = make_double2(v.x, v.y);
   }
+}
+
+// canonical [a][l][j][k] complex double -> internal [a][l][k][j] in the storage precision
+template <typename AT>
+__global__ void k_coarse_import(const double2* __restrict__ in, AT* A, int n, size_t Vc) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)81 * n * n;
+  if (t >= Vc * per) return;
+  const size_t a = t / per;
+  const int rem = (int)(t % per);
+  const int l = rem / (n * n), j = (rem / n) % n, k = rem % n;
+  const size_t dst = ((a * 81 + l) * n + k) * n + j;
+  const double2 v = in[t];
+  if constexpr (sizeof(AT) == 16) ((double2*)A)[dst] = v;
+  else if constexpr (sizeof(AT) == 8) ((float2*)A)[dst] = make_float2((float)v.x, (float)v.y);
+  else ((__half2*)A)[dst] = __halves2half2(__double2half(v.x), __double2half(v.y));
+}
+
+void coarse_import(Ctx& c, Coarse& A, const void* src, int on_device) {
+  const size_t tot = A.Vc * 81 * A.nvec * A.nvec;
+  DevMem d;
+  const double2* in = static_cast<const double2*>(src);
+  if (!on_device) {
+    d.ensure(tot * sizeof(double2));
+    HDCG_CUDA(cudaMemcpyAsync(d.p, src, tot * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    in = d.as<double2>();
+  }
+  const unsigned g = (unsigned)((tot + 255) / 256);
+  if (A.prec == HDCG_F64) k_coarse_import<double2><<<g, 256, 0, c.stream>>>(in, A.A.as<double2>(), A.nvec, A.Vc);
+  else if (A.prec == HDCG_F32) k_coarse_import<float2><<<g, 256, 0, c.stream>>>(in, A.A.as<float2>(), A.nvec, A.Vc);
+  else k_coarse_import<__half2><<<g, 256, 0, c.stream>>>(in, A.A.as<__half2>(), A.nvec, A.Vc);
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+  A.tc_ready = false;
+  A.tc_choice = -1;
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 void coarse_export(Ctx& c, const Coarse& A, void* host) {
@@ -1378,7 +1455,7 @@ template <typename AT, typename R_, int VJ>
 __device__ __forceinline__ void capply_multi_body(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
                                                   int R, const typename CV<R_>::T* __restrict__ x,
                                                   typename CV<R_>::T* ypart, size_t nc, double* dot_out,
-                                                  float2* sred) {
+                                                  typename CV<R_>::T* sred) {
   using V = typename CV<R_>::T;
   const size_t a = blockIdx.x / CGROUPS;
   const int g = blockIdx.x % CGROUPS;
@@ -1433,28 +1510,28 @@ __device__ __forceinline__ void capply_multi_body(const AT* __restrict__ A, cons
         }
     }
   }
-  // sred: [CWARPS][n][R] float2
+  // sred: [CWARPS][n][R] in the working precision
   if (ks == 0 && jp0 < NJ)
 #pragma unroll
     for (int q = 0; q < VJ; ++q)
       for (int r = 0; r < R; ++r)
-        sred[((size_t)w * n + jp0 * VJ + q) * R + r] = make_float2((float)sr[q][r], (float)si[q][r]);
+        sred[((size_t)w * n + jp0 * VJ + q) * R + r] = {sr[q][r], si[q][r]};
   if (on1)
 #pragma unroll
     for (int q = 0; q < VJ; ++q)
       for (int r = 0; r < R; ++r)
-        sred[((size_t)w * n + (jp0 + 32) * VJ + q) * R + r] = make_float2((float)sr[VJ + q][r], (float)si[VJ + q][r]);
+        sred[((size_t)w * n + (jp0 + 32) * VJ + q) * R + r] = {sr[VJ + q][r], si[VJ + q][r]};
   __syncthreads();
   for (int r = 0; r < RMAX; ++r) dot_out[r] = 0.0;
   for (int o = threadIdx.x; o < n * R; o += blockDim.x) {
-    float tr = 0, ti = 0;
+    R_ tr = 0, ti = 0;
 #pragma unroll
     for (int q = 0; q < CWARPS; ++q) {
-      const float2 v = sred[(size_t)q * n * R + o];
+      const V v = sred[(size_t)q * n * R + o];
       tr += v.x;
       ti += v.y;
     }
-    ypart[g * nc + a * n * R + o] = {(R_)tr, (R_)ti};
+    ypart[g * nc + a * n * R + o] = {tr, ti};
     const V xa = x[a * n * R + o];
     const int r = o % R;
 #pragma unroll
@@ -1480,7 +1557,7 @@ __global__ void __launch_bounds__(256) k_capply_multi(const AT* __restrict__ A, 
   extern __shared__ __align__(16) unsigned char smraw[];
   if (ctl && ctl->all_done) return;
   double dot[RMAX];
-  capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<float2*>(smraw));
+  capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<typename CV<R_>::T*>(smraw));
   if (red.result) grid_reduce<RMAX>(dot, red);
 }
 
@@ -1603,7 +1680,7 @@ static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* so
   CCtlM* ctl = A.ctl.as<CCtlM>();
   const unsigned ge = (unsigned)((ne + 255) / 256);
   const unsigned ga = (unsigned)(A.Vc * CGROUPS);
-  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(float2);
+  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(V);
   const bool vec = A.nvec % vec_width<AT>() == 0;
   auto fn = vec ? k_capply_multi<AT, R_, vec_width<AT>()> : k_capply_multi<AT, R_, 1>;
   set_smem_limit((const void*)fn, sm);
@@ -1637,6 +1714,7 @@ static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* so
 
 int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  if (coarse_tc_supported(A)) return coarse_cg_tc(c, A, R, rhs, sol, tol, maxiter);
   if (A.prec == HDCG_F64) return coarse_cg_multi_t<double2, double>(c, A, R, rhs, sol, tol, maxiter);
   if (A.prec == HDCG_F32) return coarse_cg_multi_t<float2, float>(c, A, R, rhs, sol, tol, maxiter);
   return coarse_cg_multi_t<__half2, float>(c, A, R, rhs, sol, tol, maxiter);
@@ -1654,7 +1732,7 @@ static void coarse_apply_multi_t(Ctx& c, const Coarse& A, int R, const void* x, 
   V* part = yi + nc;
   const int vp = A.vec_prec();
   cvec_convert(c, x, HDCG_F64, xi, vp, nc);
-  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(float2);
+  const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(V);
   const bool vec = A.nvec % vec_width<AT>() == 0;
   auto fn = vec ? k_capply_multi<AT, R_, vec_width<AT>()> : k_capply_multi<AT, R_, 1>;
   set_smem_limit((const void*)fn, sm);

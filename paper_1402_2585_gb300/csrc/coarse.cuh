@@ -32,9 +32,34 @@ struct Coarse {
   DevMem ctl;               // coarse CG control block (doubles + ints)
   DevMem qvec;              // restriction / coarse solution vectors of Q
   int last_iters = 8;
+  // tensor-core form (FP16 A only): A re-tiled for tcgen05, the B tiles of the
+  // current vectors, and a small state block (wait-timeout flags, per-rhs max|x|)
+  DevMem Atc, xtc, tcs;
+  bool tc_ready = false;
+  int tc_choice = -1;       // single right-hand side: -1 undecided, 0 CUDA cores, 1 tensor cores
   int vec_prec() const { return prec == HDCG_F64 ? HDCG_F64 : HDCG_F32; }
   size_t vec_bytes() const { return Vc * nvec * (vec_prec() == HDCG_F64 ? 16 : 8); }
 };
+
+// tensor-core coarse operator (coarse_tc.cu) ---------------------------------------
+struct TcState {
+  unsigned err;             // bit flags of expired pipeline waits
+  unsigned pad[3];
+  unsigned xmax[RMAX];      // per right-hand side max(|Re x|, |Im x|) as float bits
+};
+struct TcGeom {
+  int sites, MS, Kp, Rp, NS, NMMA, ncols, stages;
+  uint32_t a_bytes, b_bytes, stage_bytes;
+};
+TcGeom tc_geom(int nvec, int R);
+bool coarse_tc_supported(const Coarse& A);
+void coarse_tc_prepare(Ctx& c, Coarse& A);
+// coarse CG on R right-hand sides (FP32 vectors [a][k][r]) with the tensor-core operator
+int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+// Y = A X, x and y canonical [R][Vc][Nvec] complex double (device); F16 A on the tensor cores
+void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y64);
+// single right-hand side: time both coarse apply paths once and keep the faster
+bool coarse_use_tc_single(Ctx& c, Coarse& A);
 
 // subspace geometry (host tables -> device)
 void subspace_init(Ctx& c, Subspace& s, const int block[4], int nvec, int prec);
@@ -72,6 +97,8 @@ void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R
                    const uint4* add);
 int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
 void coarse_apply_multi(Ctx& c, const Coarse& A, int R, const void* x, void* y);
+// canonical import of A (complex double [Vc][81][j][k], host or device) into storage A.prec
+void coarse_import(Ctx& c, Coarse& A, const void* src, int on_device);
 // canonical export of A (complex double [Vc][81][j][k], host)
 void coarse_export(Ctx& c, const Coarse& A, void* host);
 

@@ -3,8 +3,11 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "context.h"
+#include "dfloat.cuh"
 
 namespace hdcg {
 
@@ -54,6 +57,14 @@ __device__ __forceinline__ void load_link(const double2*, const uint4* __restric
     const uint4 g = __ldg(p + i);
     u[2 * i] = __hiloint2double(g.y, g.x);
     u[2 * i + 1] = __hiloint2double(g.w, g.z);
+  }
+}
+__device__ __forceinline__ void load_link(const double2*, const uint4* __restrict__ p, dfl* u) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const uint4 g = __ldg(p + i);
+    u[2 * i] = dfl(__hiloint2double(g.y, g.x));
+    u[2 * i + 1] = dfl(__hiloint2double(g.w, g.z));
   }
 }
 __device__ __forceinline__ void load_link(const float2*, const uint4* __restrict__ p, float* u) {
@@ -108,9 +119,9 @@ __device__ __forceinline__ void apply_Ppow(R* v, int d, int s, int Ls, R m) {
   const int sm = DAG ? dn_src : up_src;
   const R fm = DAG ? dn_f : up_f;
 #pragma unroll
-  for (int i = 0; i < 12; ++i) v[i] = fp * __shfl_sync(FULL_MASK, v[i], sp, Ls);
+  for (int i = 0; i < 12; ++i) v[i] = fp * shfl_any(v[i], sp, Ls);
 #pragma unroll
-  for (int i = 12; i < 24; ++i) v[i] = fm * __shfl_sync(FULL_MASK, v[i], sm, Ls);
+  for (int i = 12; i < 24; ++i) v[i] = fm * shfl_any(v[i], sm, Ls);
 }
 
 // v <- a v + b P v
@@ -233,33 +244,94 @@ template <typename St, typename R, typename LT, int MU, int SF, bool KIN>
 __device__ __forceinline__ void hop_pair(const HopArgs& a, const uint4* in, const int* nbv, const uint4* lk, int s,
                                          R* acc) {
   constexpr int LG = LinkGran<LT>::g;
-  R pf[24], pb[24];
-  load_spinor<St, R>(in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
-  load_spinor<St, R>(in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
-  if (KIN) {
-    const R m = (R)a.mass;
-    apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
-    apply_lin<R, false>(pb, (R)a.b, (R)a.c, s, a.Ls, m);
+  if constexpr (std::is_same<R, dfl>::value) {
+    // double-float: compute-bound, so one neighbour at a time keeps registers low
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      R ps[24];
+      load_spinor<St, R>(in, (size_t)nbv[MU + 4 * side] * a.Ls + s, a.n5, ps);
+      if (KIN) apply_lin<R, false>(ps, (R)a.b, (R)a.c, s, a.Ls, (R)a.mass);
+      R h[12], uh[12], U[18];
+      load_link((const LT*)nullptr, lk + (MU + 4 * side) * LG, U);
+      if (side == 0) {
+        project<MU, SF>(ps, h);
+        su3_mul<R>(U, h, uh);
+        reconstruct_add<MU, SF>(uh, acc);
+      } else {
+        project<MU, -SF>(ps, h);
+        su3_mul<R>(U, h, uh);
+        reconstruct_add<MU, -SF>(uh, acc);
+      }
+    }
+  } else {
+    R pf[24], pb[24];
+    load_spinor<St, R>(in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
+    load_spinor<St, R>(in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
+    if (KIN) {
+      const R m = (R)a.mass;
+      apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
+      apply_lin<R, false>(pb, (R)a.b, (R)a.c, s, a.Ls, m);
+    }
+    R h[12], uh[12], U[18];
+    project<MU, SF>(pf, h);
+    load_link((const LT*)nullptr, lk + MU * LG, U);
+    su3_mul<R>(U, h, uh);
+    reconstruct_add<MU, SF>(uh, acc);
+    project<MU, -SF>(pb, h);
+    load_link((const LT*)nullptr, lk + (MU + 4) * LG, U);
+    su3_mul<R>(U, h, uh);
+    reconstruct_add<MU, -SF>(uh, acc);
   }
-  R h[12], uh[12], U[18];
-  project<MU, SF>(pf, h);
-  load_link((const LT*)nullptr, lk + MU * LG, U);
-  su3_mul<R>(U, h, uh);
-  reconstruct_add<MU, SF>(uh, acc);
-  project<MU, -SF>(pb, h);
-  load_link((const LT*)nullptr, lk + (MU + 4) * LG, U);
-  su3_mul<R>(U, h, uh);
-  reconstruct_add<MU, -SF>(uh, acc);
+}
+
+// hop along MU from raw (already loaded) 16-bit granules of the neighbours
+template <typename St, typename R, typename LT, int MU, int SF, bool KIN>
+__device__ __forceinline__ void hop_raw(const HopArgs& a, const uint4 (&raw)[8][3], const uint4* lk, int s, R* acc) {
+  constexpr int LG = LinkGran<LT>::g;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    R ps[24];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float t[8];
+      unpack(St{}, raw[MU + 4 * side][c], t);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ps[c * 8 + i] = (R)t[i];
+    }
+    if (KIN) apply_lin<R, false>(ps, (R)a.b, (R)a.c, s, a.Ls, (R)a.mass);
+    R h[12], uh[12], U[18];
+    load_link((const LT*)nullptr, lk + (MU + 4 * side) * LG, U);
+    if (side == 0) {
+      project<MU, SF>(ps, h);
+      su3_mul<R>(U, h, uh);
+      reconstruct_add<MU, SF>(uh, acc);
+    } else {
+      project<MU, -SF>(ps, h);
+      su3_mul<R>(U, h, uh);
+      reconstruct_add<MU, -SF>(uh, acc);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------
 // one hop pass
 // ------------------------------------------------------------------------------
+// Arithmetic type of the hop passes: FP32 for 16/32-bit storage; double-float
+// (about 48 bits, on the FP32 pipes) for FP64 storage.
+// arithmetic type of the hop: float for FP32/16-bit storage; for FP64 storage
+// either native double or (DF) a double-float pair on the FP32 pipes
+template <typename St, bool DF> struct HopCompute { using type = float; };
+template <> struct HopCompute<f64_t, false> { using type = double; };
+template <> struct HopCompute<f64_t, true> { using type = dfl; };
+
 // MINB: minimum resident CTAs per SM requested from the compiler (register
 // budget); the variants are chosen at run time by the hop autotuner.
-template <typename St, int PASS, bool MOB, int MINB>
+// PF (16-bit storage only): the raw 16-byte granules of all eight neighbour
+// spinors are loaded before any is used (24 loads in flight per thread).
+// DF (FP64 storage only): double-float arithmetic instead of FP64 units.
+template <typename St, int PASS, bool MOB, int MINB, bool PF = false, bool DF = false>
 __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
-  using R = typename Store<St>::real;
+  using R = typename HopCompute<St, DF>::type;
   using LT = typename LinkOf<St>::T;
   constexpr bool DAG = (PASS == PASS_C || PASS == PASS_D);
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,10 +355,22 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   const uint4* lk = reinterpret_cast<const uint4*>(a.links) + x4 * 8 * LinkGran<LT>::g;
   // Dh: forward (1 - g), backward (1 + g); Dh^dag flips both.
   constexpr int SF = DAG ? -1 : 1;
-  hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
-  hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+  if constexpr (PF && Store<St>::chunks == 3) {
+    uint4 raw[8][3];
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) raw[d][c] = __ldg(in + c * a.n5 + (size_t)nbv[d] * a.Ls + s);
+    hop_raw<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, raw, lk, s, acc);
+    hop_raw<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, raw, lk, s, acc);
+    hop_raw<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, raw, lk, s, acc);
+    hop_raw<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, raw, lk, s, acc);
+  } else {
+    hop_pair<St, R, LT, 0, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+    hop_pair<St, R, LT, 1, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+    hop_pair<St, R, LT, 2, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+    hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
+  }
 
   double nrm2 = 0.0;
   if (PASS == PASS_A) {
@@ -369,9 +453,11 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
 }
 
 
-constexpr int HOP_VARIANTS = 3;  // MINB = 1, 2, 3
+// MINB = 1, 2, 3; 4th (MINB 1): prefetch of all neighbours for 16-bit storage,
+// double-float arithmetic for FP64 storage
+constexpr int HOP_VARIANTS = 4;
 
-// launch variant v (0..2) of one pass for storage St
+// launch variant v (0..3) of one pass for storage St
 template <typename St>
 void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st) {
 #define HDCG_HOP_CASE(P, M)                                                      \
@@ -385,6 +471,18 @@ void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, dim3 grid, 
   HDCG_HOP_CASE(PASS_C, 1) HDCG_HOP_CASE(PASS_C, 2) HDCG_HOP_CASE(PASS_C, 3)
   HDCG_HOP_CASE(PASS_D, 1) HDCG_HOP_CASE(PASS_D, 2) HDCG_HOP_CASE(PASS_D, 3)
 #undef HDCG_HOP_CASE
+  if (v == 3) {
+    constexpr bool PF = Store<St>::chunks == 3;
+    constexpr bool DF = Store<St>::chunks == 12;
+#define HDCG_HOP_PF(P)                                                           \
+    if (pass == P) {                                                             \
+      if (mob) hop_kernel<St, P, true, 1, PF, DF><<<grid, 256, 0, st>>>(a);     \
+      else hop_kernel<St, P, false, 1, PF, DF><<<grid, 256, 0, st>>>(a);        \
+      return;                                                                    \
+    }
+    HDCG_HOP_PF(PASS_A) HDCG_HOP_PF(PASS_B) HDCG_HOP_PF(PASS_C) HDCG_HOP_PF(PASS_D)
+#undef HDCG_HOP_PF
+  }
 }
 
 // explicit instantiations live in dwf_<prec>.cu

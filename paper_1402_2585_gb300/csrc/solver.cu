@@ -632,4 +632,13 @@ void build_coarse(Ctx& c, int prec) {
   coarse_assemble(c, *c.coarse, *c.sub, prec == HDCG_F64 ? HDCG_F64 : HDCG_F32);
 }
 
+void set_coarse(Ctx& c, const void* A, int prec, int on_device) {
+  HDCG_REQUIRE(c.sub, HDCG_ERR_STATE, "no subspace (it fixes the blocking and Nvec)");
+  HDCG_REQUIRE((prec == HDCG_F64) == (c.sub->prec == HDCG_F64), HDCG_ERR_ARG,
+               "the coarse operator is FP64 exactly when the subspace is FP64");
+  if (!c.coarse) c.coarse = new Coarse();
+  coarse_init(c, *c.coarse, *c.sub, prec);
+  coarse_import(c, *c.coarse, A, on_device);
+}
+
 }  // namespace hdcg

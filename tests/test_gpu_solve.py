@@ -57,17 +57,18 @@ def test_plain_cg(small, outer, tol):
         assert st.reliable_updates >= 2
 
 
-@pytest.mark.parametrize("outer,sloppy,prec_sub,tol", [
-    (F64, F64, F64, 1e-10),
-    (F32, F32, F32, 1e-8),
-    (F32, F16, F32, 1e-8),
-    (F32, F16, F16, 1e-8),
+@pytest.mark.parametrize("outer,sloppy,prec_sub,tol,coarse", [
+    (F64, F64, F64, 1e-10, F64),
+    (F32, F32, F32, 1e-8, F32),
+    (F32, F16, F32, 1e-8, F32),
+    (F32, F16, F16, 1e-8, F32),
+    (F32, F16, F16, 1e-8, F16),
 ])
-def test_adef2_with_oracle_subspace(small, outer, sloppy, prec_sub, tol):
+def test_adef2_with_oracle_subspace(small, outer, sloppy, prec_sub, tol, coarse):
     torch, d, bl, phi, b, xs = small
     h = _handle(d, torch)
     h.set_subspace((4, 4, 4, 4), torch.from_numpy(phi).cuda(), prec=prec_sub, already_orthonormal=True)
-    h.build_coarse(F64 if prec_sub == F64 else F32)
+    h.build_coarse(coarse)
     bt = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bt)
     st = h.solve(bt, x, tol, Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=sloppy))
@@ -144,21 +145,24 @@ def _sources(d, n, seed):
     return np.stack(out)
 
 
-@pytest.mark.parametrize("alg,outer,sloppy,nrhs", [
-    (ALG_ADEF2, F32, F32, 4),
-    (ALG_ADEF2, F32, F16, 5),
-    (ALG_CG, F32, F32, 3),
-    (ALG_ADEF2, F64, F64, 2),
+@pytest.mark.parametrize("alg,outer,sloppy,nrhs,coarse", [
+    (ALG_ADEF2, F32, F32, 4, F32),
+    (ALG_ADEF2, F32, F16, 5, F32),
+    (ALG_ADEF2, F32, F16, 5, F16),
+    (ALG_ADEF2, F32, F32, 16, F16),
+    (ALG_CG, F32, F32, 3, F32),
+    (ALG_ADEF2, F64, F64, 2, F64),
 ])
-def test_batched_solve(small, alg, outer, sloppy, nrhs):
+def test_batched_solve(small, alg, outer, sloppy, nrhs, coarse):
     """Lockstep solve of several right-hand sides with uneven convergence: each
-    solution meets its true residual (oracle) and agrees with the oracle's CG."""
+    solution meets its true residual (oracle) and agrees with the oracle's CG.
+    An FP16 little Dirac operator runs the coarse CG on the tensor cores."""
     torch, d, bl, phi, b0, xs0 = small
     h = _handle(d, torch)
     if alg == ALG_ADEF2:
         h.set_subspace((4, 4, 4, 4), torch.from_numpy(phi).cuda(), prec=F64 if outer == F64 else F32,
                        already_orthonormal=True)
-        h.build_coarse(F64 if outer == F64 else F32)
+        h.build_coarse(coarse)
     tol = 1e-10 if outer == F64 else 1e-8
     B = _sources(d, nrhs, 820)
     bt = torch.from_numpy(B).cuda()
