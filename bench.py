@@ -189,6 +189,15 @@ def run_ours(args, w):
         coarse_prec = PREC[args.coarse_prec]
     h.build_coarse(coarse_prec)
     t_coarse = time.perf_counter() - t_c0
+    t_l0 = time.perf_counter()
+    ldop = None
+    if args.ldop_nvec:
+        h.build_coarse_deflation(args.ldop_nvec, inv_steps=args.ldop_steps, shift=args.ldop_shift,
+                                 tol=args.ldop_tol, maxiter=20000, seed=w.subspace_seed + 7 + rank)
+        lam = h.get_coarse_deflation(args.ldop_nvec)
+        ldop = {"nvec": args.ldop_nvec, "inv_steps": args.ldop_steps, "shift": args.ldop_shift,
+                "tol": args.ldop_tol, "ritz_min": float(lam[0]), "ritz_max": float(lam[-1])}
+    t_ldop = time.perf_counter() - t_l0
     setup_s = time.perf_counter() - t_setup0
 
     outer = 0 if prec == 0 else 1
@@ -327,7 +336,9 @@ def run_ours(args, w):
         "phases_ms_per_solve": phases,
         "hop_profile": hop_all,
         "sequential_single_rhs": seq,
+        "ldop_deflation": ldop,
         "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse,
+                          "ldop_deflation": t_ldop,
                           "inverse_iteration": {"steps": args.inv_steps, "tol": args.inv_tol}},
         "reliable_delta": args.reliable_delta,
     }
@@ -358,10 +369,12 @@ def run_apply_only(args, w):
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("profile")
     e0.record(stream)
     for _ in range(args.apply_only):
         h.apply_mdagm(x, y, prec)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     print(json.dumps({"workload": w.name, "applies": args.apply_only,
                       "ms_per_apply": e0.elapsed_time(e1) / args.apply_only}), flush=True)
@@ -386,19 +399,32 @@ def run_coarse_only(args, w):
     vc = 1
     for d, b in zip(w.dims, w.block):
         vc *= d // b
-    x = torch.view_as_real(torch.from_numpy(sy.coarse_gaussian(vc, w.nvec, 5))).to(dev).contiguous()
+    R = args.coarse_rhs
+    if R:
+        xs = sy.complex_normal(5, (R, vc, w.nvec))
+    else:
+        xs = sy.coarse_gaussian(vc, w.nvec, 5)
+    x = torch.view_as_real(torch.from_numpy(xs)).to(dev).contiguous()
     y = torch.empty_like(x)
-    h.coarse_apply(x, y)
+
+    def once():
+        if R:
+            h.coarse_apply_multi(x, y, R)
+        else:
+            h.coarse_apply(x, y)
+    once()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("profile")
     e0.record(stream)
     for _ in range(args.coarse_only):
-        h.coarse_apply(x, y)
+        once()
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
-    print(json.dumps({"workload": w.name, "coarse_applies": args.coarse_only,
+    print(json.dumps({"workload": w.name, "coarse_applies": args.coarse_only, "rhs": R or 1,
                       "coarse_storage": args.coarse_prec or w.prec,
                       "ms_per_call_device": e0.elapsed_time(e1) / args.coarse_only,
                       "ms_per_call_host": (time.perf_counter() - t0) * 1e3 / args.coarse_only}), flush=True)
@@ -417,8 +443,16 @@ def main():
     ap.add_argument("--reliable-delta", type=float, default=0.01, help="FP64 true-residual update factor")
     ap.add_argument("--coarse-prec", choices=["f64", "f32", "f16"], default=None,
                     help="storage of the little Dirac operator (default: the workload's)")
+    ap.add_argument("--ldop-nvec", type=int, default=0,
+                    help="second-level deflation vectors of the little Dirac operator (0: none)")
+    ap.add_argument("--ldop-steps", type=int, default=3, help="inverse-iteration steps of that space")
+    ap.add_argument("--ldop-shift", type=float, default=-1e-3,
+                    help="shift of those inverse-iteration steps (negative: times the mean diagonal of A)")
+    ap.add_argument("--ldop-tol", type=float, default=1e-5, help="coarse CG residual of those steps")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling case: run this many H applies only (no solve)")
+    ap.add_argument("--coarse-rhs", type=int, default=0,
+                    help="with --coarse-only: apply to this many right-hand sides at once (hdcg_coarse_apply_multi)")
     ap.add_argument("--coarse-only", type=int, default=0,
                     help="profiling case: build the coarse operator and apply it this many times")
     args = ap.parse_args()

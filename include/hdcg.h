@@ -55,6 +55,10 @@ extern "C" {
 #define HDCG_F16   2   /* IEEE half, round to nearest even */
 #define HDCG_BF16  3   /* bfloat16 (8-bit exponent, 7-bit mantissa), round to nearest even */
 #define HDCG_BF16T 4   /* bfloat16 by truncating the float32 word to its top 16 bits (Sec. 6.5) */
+#define HDCG_DF64  5   /* hdcg_apply_mpc / hdcg_apply_mdagm only: complex double buffers, operator
+                          stored and computed as double-float (hi + lo float32 pairs, about 48
+                          significant bits) on the FP32 units; the FP64-accurate operator the
+                          solver uses for its true residuals */
 
 /* return codes */
 #define HDCG_OK             0
@@ -168,6 +172,14 @@ int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
  * pipeline wait expired.  Synchronous. */
 int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
 
+/* Solve A x = b on the coarse level for nrhs (1..16) right-hand sides to the
+ * relative residual tol (at most maxiter iterations): A-DEF1 with the
+ * second-level deflation space when one was built, otherwise CG (the inner
+ * inversion of Q, Sec. 2).  b, x: canonical [nrhs][Vc][Nvec] complex double,
+ * device; x is overwritten (zero start).  *iterations (nullable) receives the
+ * lockstep iteration count.  Synchronous. */
+int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, int maxiter, int* iterations);
+
 /* y = A x exactly like hdcg_coarse_apply, but without allocating any device
  * memory: for callers that cannot call cudaMalloc on this path (for example a
  * host code that hands all device memory to its own pool allocator, or one
@@ -185,6 +197,34 @@ int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
  * race.  x, y: canonical coarse vectors, complex double, device.
  * Synchronous. */
 int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y);
+
+/* Second-level (global) deflation of the little Dirac operator (Sec. 5.2,
+ * "Little Dirac operator deflation"): nvec Gaussian start vectors (splitmix64
+ * stream seed, canonical order [k][Vc][Nvec], as for the subspace) refined by
+ * inv_steps steps of (A + shift)^-1 (coarse CG to relative residual tol, at
+ * most maxiter iterations), each followed by a global orthonormalisation
+ * (Cholesky QR, twice, FP64 Gram), then prediagonalised by Rayleigh-Ritz
+ * (dense Hermitian eigensolver on the host) so that Z^dag A Z = diag(lam).
+ * The paper uses about 128-160 vectors (Table optimised: LdopDeflVecs 160,
+ * LittleDopSolverResidualSubspace 1e-7, three shifted inverse-iteration steps).
+ * Afterwards every coarse solve is A-DEF1 with these vectors (M_1 = P_L + Q,
+ * M_2 = M_3 = 1, using the stored A Z).  nvec = 0 removes the space.  Needs an
+ * FP32 or FP16 little Dirac operator (vectors are FP32).  Synchronous. */
+typedef struct {
+    int nvec;          /* number of global deflation vectors (<= 256) */
+    int inv_steps;     /* inverse-iteration steps */
+    double shift;      /* shift of (A + shift)^-1; a negative value means |shift| times the
+                          mean diagonal element of A */
+    double tol;        /* coarse CG relative residual of each step */
+    int maxiter;       /* coarse CG iteration cap of each step */
+    uint64_t seed;     /* start vectors */
+} hdcg_ldop_params;
+
+int hdcg_build_coarse_deflation(hdcg_t h, const hdcg_ldop_params* p);
+
+/* The Ritz values lam (nvec doubles, ascending; host) and optionally the
+ * vectors Z (canonical complex double [nvec][Vc][Nvec], host; may be NULL). */
+int hdcg_get_coarse_deflation(hdcg_t h, double* lam_host, void* Z_host);
 
 /* ---------------------------------------------------------------------------
  * Solve H x = b

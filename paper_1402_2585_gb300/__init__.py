@@ -7,5 +7,5 @@ the GPU) or numpy arrays (host) are passed as raw pointers.  Importing the
 binding fails loudly when the library has not been built; there is no CPU
 fallback.
 """
-from .binding import (F16, F32, F64, BF16, BF16T, ALG_CG, ALG_ADEF2, HdcgError, Hdcg,  # noqa: F401
-                      SubspaceParams, SolveParams, SolveStats, lib, library_path, PREC_NAMES)
+from .binding import (F16, F32, F64, BF16, BF16T, DF64, ALG_CG, ALG_ADEF2, HdcgError, Hdcg,  # noqa: F401
+                      SubspaceParams, SolveParams, SolveStats, LdopParams, lib, library_path, PREC_NAMES)

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-F64, F32, F16, BF16, BF16T = 0, 1, 2, 3, 4
+F64, F32, F16, BF16, BF16T, DF64 = 0, 1, 2, 3, 4, 5
 PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "bf16t": BF16T}
 ALG_CG, ALG_ADEF2 = 0, 1
 _ERRORS = {1: "not converged", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
@@ -43,6 +43,11 @@ class SolveParams(ctypes.Structure):
                 ("mirs_iter", ctypes.c_int), ("mirs_shift", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxiter", ctypes.c_int), ("flexible", ctypes.c_int), ("maxiter", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int)]
+
+
+class LdopParams(ctypes.Structure):
+    _fields_ = [("nvec", ctypes.c_int), ("inv_steps", ctypes.c_int), ("shift", ctypes.c_double),
+                ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class SolveStats(ctypes.Structure):
@@ -76,6 +81,9 @@ _SIGS = {
     "hdcg_coarse_apply": (_I, [_P, _P, _P]),
     "hdcg_coarse_apply_noalloc": (_I, [_P, _P, _P]),
     "hdcg_coarse_apply_multi": (_I, [_P, _P, _P, _I]),
+    "hdcg_coarse_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I)]),
+    "hdcg_build_coarse_deflation": (_I, [_P, ctypes.POINTER(LdopParams)]),
+    "hdcg_get_coarse_deflation": (_I, [_P, ctypes.POINTER(_D), _P]),
     "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
     "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
     "hdcg_set_profiling": (_I, [_P, _I]),
@@ -208,6 +216,24 @@ class Hdcg:
 
     def coarse_apply_multi(self, x, y, nrhs):
         return self._check(self._L.hdcg_coarse_apply_multi(self.h, _ptr(x), _ptr(y), int(nrhs)))
+
+    def coarse_solve(self, b, x, nrhs, tol, maxiter=100000):
+        it = ctypes.c_int(0)
+        self._check(self._L.hdcg_coarse_solve(self.h, _ptr(b), _ptr(x), int(nrhs), float(tol), int(maxiter),
+                                               ctypes.byref(it)))
+        return it.value
+
+    def build_coarse_deflation(self, nvec, inv_steps=3, shift=0.0, tol=1e-7, maxiter=100000, seed=0):
+        p = LdopParams(int(nvec), int(inv_steps), float(shift), float(tol), int(maxiter), int(seed))
+        return self._check(self._L.hdcg_build_coarse_deflation(self.h, ctypes.byref(p)))
+
+    def get_coarse_deflation(self, nvec, vectors=False, shape=None):
+        """Ritz values (nvec,) and, with vectors=True, Z as complex128 of `shape`."""
+        lam = np.zeros(nvec)
+        Z = np.zeros(shape, dtype=np.complex128) if vectors else None
+        self._check(self._L.hdcg_get_coarse_deflation(
+            self.h, lam.ctypes.data_as(ctypes.POINTER(_D)), None if Z is None else ctypes.c_void_p(Z.ctypes.data)))
+        return (lam, Z) if vectors else lam
 
     def coarse_apply_noalloc(self, x, y):
         return self._check(self._L.hdcg_coarse_apply_noalloc(self.h, _ptr(x), _ptr(y)))

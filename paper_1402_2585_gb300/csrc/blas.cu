@@ -92,6 +92,14 @@ static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
 
 void canon_to_internal(Ctx& c, const void* canon, int canon_prec, uint4* out, int prec, size_t nf) {
   const unsigned g = blocks_for(c.n5 * nf);
+  if (prec == HDCG_DF64 || canon_prec == HDCG_DF64) {   // complex double canonical <-> double-float
+    HDCG_REQUIRE(prec == HDCG_DF64 && (canon_prec == HDCG_F64 || canon_prec == HDCG_DF64), HDCG_ERR_ARG,
+                 "double-float fields convert from complex double only");
+    k_canon_to_int<f64_t, df_t><<<g, 256, 0, c.stream>>>(canon, out, c.n5, nf);
+    HDCG_CUDA(cudaGetLastError());
+    ++c.launches;
+    return;
+  }
   DISPATCH_PREC(canon_prec, CT, {
     DISPATCH_PREC(prec, So, { k_canon_to_int<CT, So><<<g, 256, 0, c.stream>>>(canon, out, c.n5, nf); });
   });
@@ -101,6 +109,14 @@ void canon_to_internal(Ctx& c, const void* canon, int canon_prec, uint4* out, in
 
 void internal_to_canon(Ctx& c, const uint4* in, int prec, void* canon, int canon_prec, size_t nf) {
   const unsigned g = blocks_for(c.n5 * nf);
+  if (prec == HDCG_DF64 || canon_prec == HDCG_DF64) {
+    HDCG_REQUIRE(prec == HDCG_DF64 && (canon_prec == HDCG_F64 || canon_prec == HDCG_DF64), HDCG_ERR_ARG,
+                 "double-float fields convert to complex double only");
+    k_int_to_canon<df_t, f64_t><<<g, 256, 0, c.stream>>>(in, canon, c.n5, nf);
+    HDCG_CUDA(cudaGetLastError());
+    ++c.launches;
+    return;
+  }
   DISPATCH_PREC(prec, Si, {
     DISPATCH_PREC(canon_prec, CT, { k_int_to_canon<Si, CT><<<g, 256, 0, c.stream>>>(in, canon, c.n5, nf); });
   });
@@ -110,6 +126,14 @@ void internal_to_canon(Ctx& c, const uint4* in, int prec, void* canon, int canon
 
 void convert_field(Ctx& c, const uint4* in, int pin, uint4* out, int pout, size_t nf) {
   const unsigned g = blocks_for(c.n5 * nf);
+  if (pin == HDCG_DF64 || pout == HDCG_DF64) {   // FP64 <-> double-float only
+    if (pin == HDCG_F64 && pout == HDCG_DF64) k_convert<f64_t, df_t><<<g, 256, 0, c.stream>>>(in, out, c.n5, nf);
+    else if (pin == HDCG_DF64 && pout == HDCG_F64) k_convert<df_t, f64_t><<<g, 256, 0, c.stream>>>(in, out, c.n5, nf);
+    else throw Error{HDCG_ERR_ARG, "double-float fields convert to and from FP64 only"};
+    HDCG_CUDA(cudaGetLastError());
+    ++c.launches;
+    return;
+  }
   DISPATCH_PREC(pin, Si, {
     DISPATCH_PREC(pout, So, { k_convert<Si, So><<<g, 256, 0, c.stream>>>(in, out, c.n5, nf); });
   });

@@ -50,6 +50,10 @@ static void resolve_phases(Ctx& c) {
 static void check_prec(int prec) {
   HDCG_REQUIRE(prec >= HDCG_F64 && prec <= HDCG_BF16T, HDCG_ERR_ARG, "unknown precision code");
 }
+// the fine-operator calls also take the double-float code
+static void check_op_prec(int prec) {
+  HDCG_REQUIRE(prec >= HDCG_F64 && prec <= HDCG_DF64, HDCG_ERR_ARG, "unknown precision code");
+}
 static void check_ptr(const void* p, const char* what) {
   HDCG_REQUIRE(p != nullptr, HDCG_ERR_ARG, std::string(what) + " is NULL");
 }
@@ -148,7 +152,7 @@ int hdcg_apply_mpc(hdcg_t h, const void* in, void* out, int dagger, int prec) {
   HDCG_ENTRY(h, {
     check_ptr(in, "in");
     check_ptr(out, "out");
-    check_prec(prec);
+    check_op_prec(prec);
     HDCG_REQUIRE(in != out, HDCG_ERR_ARG, "in and out must differ");
     HDCG_REQUIRE(c.have_gauge && c.have_dwf, HDCG_ERR_STATE, "gauge field and DWF parameters required");
     c.canon_in.ensure(c.field_bytes(prec));
@@ -164,7 +168,7 @@ int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp)
   HDCG_ENTRY(h, {
     check_ptr(in, "in");
     check_ptr(out, "out");
-    check_prec(prec);
+    check_op_prec(prec);
     HDCG_REQUIRE(in != out, HDCG_ERR_ARG, "in and out must differ");
     HDCG_REQUIRE(c.have_gauge && c.have_dwf, HDCG_ERR_STATE, "gauge field and DWF parameters required");
     c.canon_in.ensure(c.field_bytes(prec));
@@ -318,6 +322,37 @@ int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs) {
   return HDCG_OK;
 }
 
+int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, int maxiter, int* iterations) {
+  HDCG_ENTRY(h, {
+    check_ptr(b, "b");
+    check_ptr(x, "x");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    HDCG_REQUIRE(nrhs >= 1 && nrhs <= RMAX, HDCG_ERR_ARG, "nrhs must be 1..16");
+    HDCG_REQUIRE(tol > 0 && maxiter > 0, HDCG_ERR_ARG, "tol > 0 and maxiter > 0");
+    const int it = coarse_solve_canon(c, *c.coarse, nrhs, b, x, tol, maxiter);
+    if (iterations) *iterations = it;
+  });
+  return HDCG_OK;
+}
+
+int hdcg_build_coarse_deflation(hdcg_t h, const hdcg_ldop_params* p) {
+  HDCG_ENTRY(h, {
+    check_ptr(p, "params");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    ldop_build(c, *c.coarse, *p);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_get_coarse_deflation(hdcg_t h, double* lam_host, void* Z_host) {
+  HDCG_ENTRY(h, {
+    check_ptr(lam_host, "lam");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    ldop_export(c, *c.coarse, lam_host, Z_host);
+  });
+  return HDCG_OK;
+}
+
 int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y) {
   HDCG_ENTRY(h, {
     check_ptr(x, "x");
@@ -394,7 +429,7 @@ int hdcg_set_profiling(hdcg_t h, int on) {
 
 int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes) {
   HDCG_ENTRY(h, {
-    check_prec(prec);
+    check_op_prec(prec);
     resolve_profile(c);
     if (launches) *launches = c.prof.launches[prec];
     if (total_ms) *total_ms = c.prof.ms[prec];

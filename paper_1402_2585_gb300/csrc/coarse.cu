@@ -112,6 +112,24 @@ __global__ void k_noise(uint4* vecs, size_t n5, size_t nf, uint64_t seed) {
   store_spinor<S, R>(vecs + f * n5 * Store<S>::chunks, site5, n5, v);
 }
 
+// n complex Gaussians (E|z|^2 = 1) in canonical order, element e from outputs 2e, 2e+1
+__global__ void k_noise_c(float2* out, size_t n, uint64_t seed) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double u1 = u01(splitmix64_at(seed, 2 * t));
+  const double u2 = u01(splitmix64_at(seed, 2 * t + 1));
+  const double r = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  out[t] = make_float2((float)(r * cs), (float)(r * sn));
+}
+
+void coarse_noise(Ctx& c, float2* out, size_t n, uint64_t seed) {
+  k_noise_c<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(out, n, seed);
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+}
+
 void subspace_noise(Ctx& c, Subspace& s, uint64_t seed) {
   const size_t n = c.n5 * s.nvec;
   DISPATCH_SUB(s.prec, S, { k_noise<S><<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(s.vecs.as<uint4>(), c.n5, s.nvec, seed); });
@@ -575,6 +593,8 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   A.prec = prec;
   A.tc_ready = false;
   A.tc_choice = -1;
+  A.defl.nd = 0;            // a deflation space belongs to the operator it was built for
+  A.defl.lam_h.clear();
   A.nvec = s.nvec;
   A.Vc = s.Vc;
   std::vector<int> nb(s.Vc * 81);
@@ -1175,6 +1195,10 @@ bool coarse_use_tc_single(Ctx& c, Coarse& A) {
 }
 
 int coarse_cg(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter) {
+  if (A.defl.nd > 0) {
+    if (coarse_tc_supported(A) && A.tc_choice < 0) tune_single(c, A, rhs, sol);
+    return coarse_adef1(c, A, 1, rhs, sol, tol, maxiter);
+  }
   if (coarse_tc_supported(A)) {
     if (A.tc_choice < 0) tune_single(c, A, rhs, sol);
     if (A.tc_choice == 1) return coarse_cg_tc(c, A, 1, rhs, sol, tol, maxiter);
@@ -1455,7 +1479,7 @@ template <typename AT, typename R_, int VJ>
 __device__ __forceinline__ void capply_multi_body(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
                                                   int R, const typename CV<R_>::T* __restrict__ x,
                                                   typename CV<R_>::T* ypart, size_t nc, double* dot_out,
-                                                  typename CV<R_>::T* sred) {
+                                                  typename CV<R_>::T* sred, R_ shift) {
   using V = typename CV<R_>::T;
   const size_t a = blockIdx.x / CGROUPS;
   const int g = blockIdx.x % CGROUPS;
@@ -1531,8 +1555,12 @@ __device__ __forceinline__ void capply_multi_body(const AT* __restrict__ A, cons
       tr += v.x;
       ti += v.y;
     }
-    ypart[g * nc + a * n * R + o] = {tr, ti};
     const V xa = x[a * n * R + o];
+    if (g == 0) {   // (A + shift) x: the shift enters once, with the first group
+      tr += shift * xa.x;
+      ti += shift * xa.y;
+    }
+    ypart[g * nc + a * n * R + o] = {tr, ti};
     const int r = o % R;
 #pragma unroll
     for (int rr = 0; rr < RMAX; ++rr)
@@ -1552,12 +1580,13 @@ struct CCtlM {
 template <typename AT, typename R_, int VJ>
 __global__ void __launch_bounds__(256) k_capply_multi(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
                                                       int R, const typename CV<R_>::T* __restrict__ x,
-                                                      typename CV<R_>::T* ypart, size_t nc, const CCtlM* ctl,
-                                                      Reduction red) {
+                                                      typename CV<R_>::T* ypart, size_t nc, const int* skip,
+                                                      Reduction red, R_ shift) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  if (ctl && ctl->all_done) return;
+  if (skip && *skip) return;
   double dot[RMAX];
-  capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<typename CV<R_>::T*>(smraw));
+  capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<typename CV<R_>::T*>(smraw),
+                                shift);
   if (red.result) grid_reduce<RMAX>(dot, red);
 }
 
@@ -1668,7 +1697,8 @@ __global__ void k_ccgm_check(CCtlM* ctl, int R, int par, int maxiter) {
 }
 
 template <typename AT, typename R_>
-static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
+static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter,
+                             double shift) {
   using V = typename CV<R_>::T;
   const size_t ne = A.Vc * A.nvec;   // coarse site-vector elements per right-hand side
   const size_t nc = ne * R;
@@ -1694,8 +1724,8 @@ static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* so
   while (true) {
     for (int bq = 0; bq < batch && queued < maxiter; ++bq, ++queued) {
       const int par = queued & 1;
-      fn<<<ga, 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, p, w, nc, ctl,
-                                    make_reduction(c, ga, RMAX, &ctl->pAp[0], 0));
+      fn<<<ga, 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, p, w, nc, &ctl->all_done,
+                                    make_reduction(c, ga, RMAX, &ctl->pAp[0], 0), (R_)shift);
       k_ccgm_update<R_><<<ge, 256, 0, c.stream>>>((V*)sol, r, p, w, ne, R, nc, ctl, par,
                                                   make_reduction(c, ge, RMAX, &ctl->rr[par ^ 1][0], 0));
       k_ccgm_p<R_><<<ge, 256, 0, c.stream>>>(p, r, ne, R, ctl, par, maxiter);
@@ -1712,12 +1742,56 @@ static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* so
   return h.iter;
 }
 
-int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
+int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter, double shift,
+                    bool deflate) {
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
-  if (coarse_tc_supported(A)) return coarse_cg_tc(c, A, R, rhs, sol, tol, maxiter);
-  if (A.prec == HDCG_F64) return coarse_cg_multi_t<double2, double>(c, A, R, rhs, sol, tol, maxiter);
-  if (A.prec == HDCG_F32) return coarse_cg_multi_t<float2, float>(c, A, R, rhs, sol, tol, maxiter);
-  return coarse_cg_multi_t<__half2, float>(c, A, R, rhs, sol, tol, maxiter);
+  if (deflate && A.defl.nd > 0 && shift == 0.0) return coarse_adef1(c, A, R, rhs, sol, tol, maxiter);
+  if (coarse_tc_supported(A)) return coarse_cg_tc(c, A, R, rhs, sol, tol, maxiter, shift);
+  if (A.prec == HDCG_F64) return coarse_cg_multi_t<double2, double>(c, A, R, rhs, sol, tol, maxiter, shift);
+  if (A.prec == HDCG_F32) return coarse_cg_multi_t<float2, float>(c, A, R, rhs, sol, tol, maxiter, shift);
+  return coarse_cg_multi_t<__half2, float>(c, A, R, rhs, sol, tol, maxiter, shift);
+}
+
+// single right-hand side, skipped while *skip is nonzero
+template <typename AT, typename R, int VJ>
+__global__ void __launch_bounds__(256) k_capply_skip(const AT* __restrict__ A, const int* __restrict__ cnbr, int n,
+                                                     const typename CV<R>::T* __restrict__ x,
+                                                     typename CV<R>::T* ypart, size_t nc, const int* skip,
+                                                     Reduction red) {
+  if (skip && *skip) return;
+  double dv = 0.0;
+  capply_body<AT, R, VJ>(A, cnbr, n, x, ypart, nc, &dv);
+  double v[1] = {dv};
+  grid_reduce<1>(v, red);
+}
+
+template <typename AT>
+static int coarse_apply_partials_t(Ctx& c, const Coarse& A, int R, const float2* p, float2* wpart, const int* skip,
+                                   double* pAp) {
+  const size_t nc = A.Vc * A.nvec * (size_t)R;
+  const unsigned ga = (unsigned)(A.Vc * CGROUPS);
+  const bool vec = A.nvec % vec_width<AT>() == 0;
+  if (R == 1) {
+    auto fn = vec ? k_capply_skip<AT, float, vec_width<AT>()> : k_capply_skip<AT, float, 1>;
+    fn<<<ga, 256, 0, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, p, wpart, nc, skip,
+                                 make_reduction(c, ga, 1, pAp, 0));
+  } else {
+    const size_t sm = (size_t)CWARPS * A.nvec * R * sizeof(float2);
+    auto fn = vec ? k_capply_multi<AT, float, vec_width<AT>()> : k_capply_multi<AT, float, 1>;
+    set_smem_limit((const void*)fn, sm);
+    fn<<<ga, 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, p, wpart, nc, skip,
+                                  make_reduction(c, ga, RMAX, pAp, 0), 0.f);
+  }
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+  return CGROUPS;
+}
+
+int coarse_apply_partials(Ctx& c, const Coarse& A, int R, const float2* p, float2* wpart, const int* skip,
+                          double* pAp) {
+  HDCG_REQUIRE(A.prec == HDCG_F32 || A.prec == HDCG_F16, HDCG_ERR_ARG, "FP32 or FP16 coarse operator");
+  if (A.prec == HDCG_F32) return coarse_apply_partials_t<float2>(c, A, R, p, wpart, skip, pAp);
+  return coarse_apply_partials_t<__half2>(c, A, R, p, wpart, skip, pAp);
 }
 
 // Y = A X for R right-hand sides (canonical [a][k][r] complex double in and out)
@@ -1738,7 +1812,7 @@ static void coarse_apply_multi_t(Ctx& c, const Coarse& A, int R, const void* x, 
   set_smem_limit((const void*)fn, sm);
   Reduction none{};
   fn<<<(unsigned)(A.Vc * CGROUPS), 256, sm, c.stream>>>(A.A.as<AT>(), A.cnbr.as<int>(), A.nvec, R, xi, part, nc,
-                                                         nullptr, none);
+                                                         nullptr, none, (R_)0);
   k_sum_groups<R_><<<(unsigned)((nc + 255) / 256), 256, 0, c.stream>>>(part, yi, nc);
   c.launches += 2;
   cvec_convert(c, yi, vp, y, HDCG_F64, nc);

@@ -37,6 +37,14 @@ struct Coarse {
   DevMem Atc, xtc, tcs;
   bool tc_ready = false;
   int tc_choice = -1;       // single right-hand side: -1 undecided, 0 CUDA cores, 1 tensor cores
+  // second-level (global) deflation space of A, prediagonalised: Z^dag A Z = diag(lam)
+  struct Defl {
+    int nd = 0;
+    DevMem Z;               // [nd][Vc*Nvec] complex float
+    DevMem W;               // [nd][Vc*Nvec] complex float: Z - A Z
+    DevMem lam;             // [nd] double
+    std::vector<double> lam_h;
+  } defl;
   int vec_prec() const { return prec == HDCG_F64 ? HDCG_F64 : HDCG_F32; }
   size_t vec_bytes() const { return Vc * nvec * (vec_prec() == HDCG_F64 ? 16 : 8); }
 };
@@ -55,9 +63,19 @@ TcGeom tc_geom(int nvec, int R);
 bool coarse_tc_supported(const Coarse& A);
 void coarse_tc_prepare(Ctx& c, Coarse& A);
 // coarse CG on R right-hand sides (FP32 vectors [a][k][r]) with the tensor-core operator
-int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter,
+                 double shift = 0.0);
+// building blocks of the tensor-core apply (x, y FP32 [a][k][r]; xmax per-rhs max|x| bits)
+void coarse_tc_max(Ctx& c, const float2* x, size_t ne, int R, unsigned* xmax);
+void coarse_tc_to_b(Ctx& c, Coarse& A, int R, const float2* x, const unsigned* xmax, const int* skip);
+void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
+                     double* dot_result, double shift);
+void coarse_tc_check(Ctx& c, Coarse& A);
 // Y = A X, x and y canonical [R][Vc][Nvec] complex double (device); F16 A on the tensor cores
 void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y64);
+// coarse solve A x = b for R right-hand sides, b and x canonical [R][Vc][Nvec] complex
+// double (device); A-DEF1 when a deflation space exists, else CG; returns iterations
+int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, double tol, int maxiter);
 // single right-hand side: time both coarse apply paths once and keep the faster
 bool coarse_use_tc_single(Ctx& c, Coarse& A);
 
@@ -95,7 +113,21 @@ void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64);
 void restrict_multi(Ctx& c, const Subspace& s, const uint4* v, int vprec, int R, void* cvec, int cprec);
 void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R, uint4* out, int oprec,
                    const uint4* add);
-int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+// coarse CG on (A + shift) for R right-hand sides; with deflate and a second-level
+// deflation space (and no shift) the solve is A-DEF1 instead
+int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter,
+                    double shift = 0.0, bool deflate = true);
+// y partials of (A) p on the CUDA cores for a coarse FP32/FP16 operator and FP32
+// vectors [a][k][r]; returns the number of partial products (consumers add them);
+// per-rhs <p, A p> into pAp; nothing happens while *skip is nonzero
+int coarse_apply_partials(Ctx& c, const Coarse& A, int R, const float2* p, float2* wpart, const int* skip,
+                          double* pAp);
+// second-level deflation of the little Dirac operator (ldop.cu)
+void ldop_build(Ctx& c, Coarse& A, const hdcg_ldop_params& prm);
+void ldop_export(Ctx& c, const Coarse& A, double* lam_host, void* Z_host);
+int coarse_adef1(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+// n complex Gaussians, splitmix64 stream seed, canonical order (same stream as subspace_noise)
+void coarse_noise(Ctx& c, float2* out, size_t n, uint64_t seed);
 void coarse_apply_multi(Ctx& c, const Coarse& A, int R, const void* x, void* y);
 // canonical import of A (complex double [Vc][81][j][k], host or device) into storage A.prec
 void coarse_import(Ctx& c, Coarse& A, const void* src, int on_device);

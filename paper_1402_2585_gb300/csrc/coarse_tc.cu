@@ -184,6 +184,7 @@ struct TcArgs {
   unsigned* err;       // bit flags of expired waits
   int Vc, n, R, sites, MS, Kp, NS, stages, ncols;
   uint32_t a_bytes, b_bytes, idesc;
+  float shift;         // Y = (A + shift) X (needs x)
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction red) {
@@ -327,11 +328,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
           const float P = d[4 * r] + d[4 * r + 2];
           const float Q = d[4 * r + 1] + d[4 * r + 3];
           const float t = __shfl_xor_sync(FULL_MASK, Q, 1);
-          const float v = (ri ? t + P : P - t) * inv[r];
+          float v = (ri ? t + P : P - t) * inv[r];
           if (valid) {
             const size_t e = ((size_t)site * g.n + j) * g.R + r;
+            if (g.x) {
+              const float xv = reinterpret_cast<const float*>(g.x)[2 * e + ri];
+              v += g.shift * xv;
+              dot[r] += (double)xv * (double)v;
+            }
             reinterpret_cast<float*>(g.y)[2 * e + ri] = v;
-            if (g.x) dot[r] += (double)reinterpret_cast<const float*>(g.x)[2 * e + ri] * (double)v;
           }
         }
       }
@@ -398,7 +403,7 @@ void coarse_tc_to_b(Ctx& c, Coarse& A, int R, const float2* x, const unsigned* x
 }
 
 void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
-                     double* dot_result) {
+                     double* dot_result, double shift) {
   const TcGeom g = tc_geom(A.nvec, R);
   TcArgs a;
   a.Atc = A.Atc.as<uint4>();
@@ -421,6 +426,7 @@ void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const
   a.a_bytes = g.a_bytes;
   a.b_bytes = g.b_bytes;
   a.idesc = tc::idesc_f16_f32(128, g.NMMA);
+  a.shift = (float)shift;
   const size_t smem = (size_t)g.stages * g.stage_bytes + (2 * g.stages + 3) * 8 + 16;
   static size_t smem_set = 0;
   if (smem > smem_set) {
@@ -576,7 +582,7 @@ __global__ void k_cgt_check(CCtlT* ctl, int R, int par, int maxiter) {
   ctl->all_done = all;
 }
 
-int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter) {
+int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter, double shift) {
   coarse_tc_prepare(c, A);
   const size_t ne = A.Vc * A.nvec;
   const size_t nc = ne * R;
@@ -601,7 +607,7 @@ int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
     for (int bq = 0; bq < batch && queued < maxiter; ++bq, ++queued) {
       const int par = queued & 1;
       coarse_tc_to_b(c, A, R, p, xmax, skip);
-      coarse_tc_apply(c, A, R, p, w, xmax, skip, &ctl->pAp[0]);
+      coarse_tc_apply(c, A, R, p, w, xmax, skip, &ctl->pAp[0], shift);
       k_cgt_update<<<ge, 256, 0, c.stream>>>((float2*)sol, r, p, w, ne, R, ctl, par, xmax,
                                              make_reduction(c, ge, RMAX, &ctl->rr[par ^ 1][0], 0));
       k_cgt_p<<<ge, 256, 0, c.stream>>>(p, r, ne, R, ctl, par, xmax);
@@ -641,6 +647,33 @@ __global__ void k_multi_to_canon(const V* __restrict__ in, double2* out, size_t 
   out[(size_t)r * ne + e] = make_double2((double)in[t].x, (double)in[t].y);
 }
 
+int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, double tol, int maxiter) {
+  HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  const size_t ne = A.Vc * A.nvec, nc = ne * R;
+  const unsigned gt = (unsigned)((nc + 255) / 256);
+  DevMem tmp;
+  int it;
+  if (A.vec_prec() == HDCG_F32) {
+    tmp.ensure(2 * nc * sizeof(float2));
+    float2* bi = tmp.as<float2>();
+    float2* xi = bi + nc;
+    k_canon_to_multi<float2><<<gt, 256, 0, c.stream>>>((const double2*)b64, bi, ne, R);
+    it = coarse_cg_multi(c, A, R, bi, xi, tol, maxiter);
+    k_multi_to_canon<float2><<<gt, 256, 0, c.stream>>>(xi, (double2*)x64, ne, R);
+  } else {
+    tmp.ensure(2 * nc * sizeof(double2));
+    double2* bi = tmp.as<double2>();
+    double2* xi = bi + nc;
+    k_canon_to_multi<double2><<<gt, 256, 0, c.stream>>>((const double2*)b64, bi, ne, R);
+    it = coarse_cg_multi(c, A, R, bi, xi, tol, maxiter);
+    k_multi_to_canon<double2><<<gt, 256, 0, c.stream>>>(xi, (double2*)x64, ne, R);
+  }
+  c.launches += 2;
+  HDCG_CUDA(cudaGetLastError());
+  HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  return it;
+}
+
 void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y64) {
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   const size_t ne = A.Vc * A.nvec, nc = ne * R;
@@ -655,7 +688,7 @@ void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y
     unsigned* xmax = A.tcs.as<TcState>()->xmax;
     coarse_tc_max(c, xi, ne, R, xmax);
     coarse_tc_to_b(c, A, R, xi, xmax, nullptr);
-    coarse_tc_apply(c, A, R, xi, yi, xmax, nullptr, nullptr);
+    coarse_tc_apply(c, A, R, xi, yi, xmax, nullptr, nullptr, 0.0);
     k_multi_to_canon<float2><<<gt, 256, 0, c.stream>>>(yi, (double2*)y64, ne, R);
     c.launches += 2;
     HDCG_CUDA(cudaGetLastError());

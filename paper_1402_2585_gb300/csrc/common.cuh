@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace hdcg {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
@@ -25,6 +27,7 @@ struct f32_t {};
 struct f16_t {};
 struct bf16_t {};
 struct bf16t_t {};  // bfloat16 by truncation of the float32 word
+struct df_t {};     // double-float: (hi, lo) float32 pairs
 
 template <typename St> struct Store;
 template <> struct Store<f64_t> {
@@ -44,6 +47,12 @@ template <> struct Store<f16_t> {
   static constexpr int per_chunk = 8;
   static constexpr int chunks = 3;
   static constexpr int bytes_per_real = 2;
+};
+template <> struct Store<df_t> {
+  using real = dfl;
+  static constexpr int per_chunk = 2;
+  static constexpr int chunks = 12;
+  static constexpr int bytes_per_real = 8;
 };
 template <> struct Store<bf16_t> : Store<f16_t> {};
 template <> struct Store<bf16t_t> : Store<f16_t> {};
@@ -78,6 +87,10 @@ __device__ __forceinline__ void unpack(bf16_t, const uint4& g, float* r) {
   r[4] = c.x; r[5] = c.y; r[6] = d.x; r[7] = d.y;
 }
 __device__ __forceinline__ void unpack(bf16t_t, const uint4& g, float* r) { unpack(bf16_t{}, g, r); }
+__device__ __forceinline__ void unpack(df_t, const uint4& g, dfl* r) {
+  r[0] = dfl(__uint_as_float(g.x), __uint_as_float(g.y));
+  r[1] = dfl(__uint_as_float(g.z), __uint_as_float(g.w));
+}
 
 // pack per_chunk reals into one granule ---------------------------------------
 __device__ __forceinline__ uint4 pack(f64_t, const double* r) {
@@ -101,6 +114,10 @@ __device__ __forceinline__ unsigned f2b2(float a, float b) {
 __device__ __forceinline__ unsigned f2b2t(float a, float b) {
   // keep sign, 8-bit exponent and top 7 mantissa bits of each float32 word
   return (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xffff0000u);
+}
+__device__ __forceinline__ uint4 pack(df_t, const dfl* r) {
+  return make_uint4(__float_as_uint(r[0].hi), __float_as_uint(r[0].lo), __float_as_uint(r[1].hi),
+                    __float_as_uint(r[1].lo));
 }
 __device__ __forceinline__ uint4 pack(f16_t, const float* r) {
   return make_uint4(f2h2(r[0], r[1]), f2h2(r[2], r[3]), f2h2(r[4], r[5]), f2h2(r[6], r[7]));
@@ -180,8 +197,9 @@ struct Reduction {
   int result_stride;    // doubles between the results of consecutive right-hand sides
 };
 
+// Returns true in every thread of the last block (after the totals are stored).
 template <int NV>
-__device__ void grid_reduce(double (&v)[NV], const Reduction& red) {
+__device__ bool grid_reduce(double (&v)[NV], const Reduction& red) {
   block_sum<NV>(v);
   __shared__ bool last;
   const unsigned y = blockIdx.y;
@@ -196,7 +214,7 @@ __device__ void grid_reduce(double (&v)[NV], const Reduction& red) {
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   double acc[NV];
 #pragma unroll
@@ -210,6 +228,7 @@ __device__ void grid_reduce(double (&v)[NV], const Reduction& red) {
     for (int i = 0; i < NV; ++i) result[i] = red.accumulate ? result[i] + acc[i] : acc[i];
     *ticket = 0;
   }
+  return true;
 }
 
 }  // namespace hdcg

@@ -31,8 +31,12 @@ struct Error {
   } while (0)
 
 inline bool is_16bit(int prec) { return prec == HDCG_F16 || prec == HDCG_BF16 || prec == HDCG_BF16T; }
-inline size_t bytes_per_real(int prec) { return prec == HDCG_F64 ? 8 : prec == HDCG_F32 ? 4 : 2; }
-inline int link_slot(int prec) { return prec == HDCG_BF16T ? HDCG_BF16 : prec; }
+inline size_t bytes_per_real(int prec) {
+  return (prec == HDCG_F64 || prec == HDCG_DF64) ? 8 : prec == HDCG_F32 ? 4 : 2;
+}
+// link storage slots: F64, F32, F16, BF16 (also BF16T), double-float
+inline int link_slot(int prec) { return prec == HDCG_BF16T ? HDCG_BF16 : prec == HDCG_DF64 ? 4 : prec; }
+constexpr int NPREC = 6;   // precision codes 0..5 (HDCG_F64 .. HDCG_DF64)
 
 // device memory owned by the handle ----------------------------------------------
 struct DevMem {
@@ -82,9 +86,9 @@ struct HopProfile {
   bool on = false;
   std::vector<cudaEvent_t> pending;  // (start, stop) pairs, recorded on the stream
   std::vector<int> pending_prec;
-  long long launches[5] = {0, 0, 0, 0, 0};
-  double ms[5] = {0, 0, 0, 0, 0};
-  double bytes[5] = {0, 0, 0, 0, 0};
+  long long launches[NPREC] = {};
+  double ms[NPREC] = {};
+  double bytes[NPREC] = {};
 };
 
 // solve-phase timing (CUDA events on the stream, resolved on request)
@@ -109,8 +113,8 @@ struct Ctx {
   DwfCoeffs co;
 
   DevMem nbr[2];          // int32 [n4][8]: neighbour cb index of output site x (parity p)
-  DevMem links[4][2];     // per link slot (F64, F32, F16, BF16) and output parity
-  DevMem scratch_f[5][24]; // work fields per precision (slot roles: solver.cu; 20-23: hop autotuner)
+  DevMem links[5][2];     // per link slot (F64, F32, F16, BF16) and output parity
+  DevMem scratch_f[NPREC][24]; // work fields per precision (slot roles: solver.cu; 20-23: hop autotuner)
   std::map<int, int> hop_tuned;  // (prec, pass, fused, reduction) -> chosen hop variant
   bool tuning_off = false;
   DevMem red_partials, red_ticket, scalars;

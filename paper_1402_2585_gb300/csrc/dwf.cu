@@ -66,7 +66,7 @@ __global__ void nbr_kernel(Geom g, int* nbr) {
 // links[p][i][dir][3][3]: dir < 4: U_mu(x); dir >= 4: U_mu(x - mu)^dag; the
 // antiperiodic time boundary is folded in as a sign.
 __global__ void link_kernel(Geom g, int apbc, const double2* __restrict__ U, double2* l64,
-                            float2* l32, __half2* l16, __nv_bfloat162* lb16) {
+                            float2* l32, __half2* l16, __nv_bfloat162* lb16, float4* ldf) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n4) return;
   int x[4];
@@ -93,6 +93,9 @@ __global__ void link_kernel(Geom g, int apbc, const double2* __restrict__ U, dou
         l32[(i * 8 + dir) * 10 + e] = make_float2((float)v.x, (float)v.y);
         l16[(i * 8 + dir) * 12 + e] = __floats2half2_rn((float)v.x, (float)v.y);
         lb16[(i * 8 + dir) * 12 + e] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        ldf[(i * 8 + dir) * 9 + e] =
+            make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
       }
   }
 }
@@ -129,12 +132,14 @@ void dwf_upload_gauge(Ctx& c, const void* U, bool on_device) {
     c.links[HDCG_F32][p].ensure(nl * 10 * sizeof(float2));
     c.links[HDCG_F16][p].ensure(nl * 12 * sizeof(__half2));
     c.links[HDCG_BF16][p].ensure(nl * 12 * sizeof(__nv_bfloat162));
+    c.links[link_slot(HDCG_DF64)][p].ensure(nl * 9 * sizeof(float4));
     HDCG_CUDA(cudaMemsetAsync(c.links[HDCG_F32][p].p, 0, nl * 10 * sizeof(float2), c.stream));
     HDCG_CUDA(cudaMemsetAsync(c.links[HDCG_F16][p].p, 0, nl * 12 * sizeof(__half2), c.stream));
     HDCG_CUDA(cudaMemsetAsync(c.links[HDCG_BF16][p].p, 0, nl * 12 * sizeof(__nv_bfloat162), c.stream));
     link_kernel<<<(unsigned)((c.n4 + 255) / 256), 256, 0, c.stream>>>(
         geom(c, p), c.apbc, src, c.links[HDCG_F64][p].as<double2>(), c.links[HDCG_F32][p].as<float2>(),
-        c.links[HDCG_F16][p].as<__half2>(), c.links[HDCG_BF16][p].as<__nv_bfloat162>());
+        c.links[HDCG_F16][p].as<__half2>(), c.links[HDCG_BF16][p].as<__nv_bfloat162>(),
+        c.links[link_slot(HDCG_DF64)][p].as<float4>());
     HDCG_CUDA(cudaGetLastError());
     ++c.launches;
   }
@@ -180,6 +185,7 @@ static void dispatch_hop(int prec, int v, int pass, bool mob, const HopArgs& a, 
     case HDCG_F16: launch_hop_f16(v, pass, mob, a, grid, st); break;
     case HDCG_BF16: launch_hop_bf16(v, pass, mob, a, grid, st); break;
     case HDCG_BF16T: launch_hop_bf16t(v, pass, mob, a, grid, st); break;
+    case HDCG_DF64: launch_hop_df(v, pass, mob, a, grid, st); break;
     default: throw Error{HDCG_ERR_ARG, "unknown precision code"};
   }
 }

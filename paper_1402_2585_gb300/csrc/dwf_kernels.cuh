@@ -47,6 +47,7 @@ struct HopArgs {
 // ------------------------------------------------------------------------------
 template <typename LT> struct LinkGran;
 template <> struct LinkGran<double2> { static constexpr int g = 9; };
+template <> struct LinkGran<float4> { static constexpr int g = 9; };   // double-float (re hi, re lo, im hi, im lo)
 template <> struct LinkGran<float2> { static constexpr int g = 5; };
 template <> struct LinkGran<__half2> { static constexpr int g = 3; };
 template <> struct LinkGran<__nv_bfloat162> { static constexpr int g = 3; };
@@ -57,6 +58,14 @@ __device__ __forceinline__ void load_link(const double2*, const uint4* __restric
     const uint4 g = __ldg(p + i);
     u[2 * i] = __hiloint2double(g.y, g.x);
     u[2 * i + 1] = __hiloint2double(g.w, g.z);
+  }
+}
+__device__ __forceinline__ void load_link(const float4*, const uint4* __restrict__ p, dfl* u) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const uint4 g = __ldg(p + i);
+    u[2 * i] = dfl(__uint_as_float(g.x), __uint_as_float(g.y));
+    u[2 * i + 1] = dfl(__uint_as_float(g.z), __uint_as_float(g.w));
   }
 }
 __device__ __forceinline__ void load_link(const double2*, const uint4* __restrict__ p, dfl* u) {
@@ -232,6 +241,7 @@ __device__ __forceinline__ void su3_mul(const R* U, const R* h, R* uh) {
 
 template <typename St> struct LinkOf;
 template <> struct LinkOf<f64_t> { using T = double2; };
+template <> struct LinkOf<df_t> { using T = float4; };
 template <> struct LinkOf<f32_t> { using T = float2; };
 template <> struct LinkOf<f16_t> { using T = __half2; };
 template <> struct LinkOf<bf16_t> { using T = __nv_bfloat162; };
@@ -323,6 +333,7 @@ __device__ __forceinline__ void hop_raw(const HopArgs& a, const uint4 (&raw)[8][
 template <typename St, bool DF> struct HopCompute { using type = float; };
 template <> struct HopCompute<f64_t, false> { using type = double; };
 template <> struct HopCompute<f64_t, true> { using type = dfl; };
+template <bool DF> struct HopCompute<df_t, DF> { using type = dfl; };
 
 // MINB: minimum resident CTAs per SM requested from the compiler (register
 // budget); the variants are chosen at run time by the hop autotuner.
@@ -491,5 +502,6 @@ void launch_hop_f32(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cuda
 void launch_hop_f16(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
 void launch_hop_bf16(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
 void launch_hop_bf16t(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
+void launch_hop_df(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st);
 
 }  // namespace hdcg

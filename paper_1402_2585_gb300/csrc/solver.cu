@@ -205,11 +205,24 @@ static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdc
 }
 
 // r64 = b - H64 x_hi; returns |r64|^2 (host), r (op) = r64
+// r64 = b64 - H x64 for R right-hand sides with the double-float operator (FP64
+// accuracy on the FP32 units): x and b enter as double-float copies, r leaves as FP64
+static void residual_df(Ctx& c, int R, const uint4* b64, const uint4* x64, uint4* r64) {
+  uint4* xd = c.scratch(HDCG_DF64, 5, R);
+  uint4* bd = c.scratch(HDCG_DF64, 6, R);
+  uint4* rd = c.scratch(HDCG_DF64, 7, R);
+  convert_field(c, x64, HDCG_F64, xd, HDCG_DF64, R);
+  convert_field(c, b64, HDCG_F64, bd, HDCG_DF64, R);
+  if (R == 1) apply_mdagm(c, HDCG_DF64, xd, rd, nullptr, -1.0, 1.0, bd);
+  else apply_mdagm_multi(c, HDCG_DF64, R, xd, rd, nullptr, -1.0, 1.0, bd);
+  convert_field(c, rd, HDCG_DF64, r64, HDCG_F64, R);
+}
+
 static double true_residual(Ctx& c, int op, const uint4* b64, const uint4* xhi, uint4* r, hdcg_stats* st) {
   uint4* r64 = c.scratch(HDCG_F64, SL_R64);
   {
     PhaseTimer pt(c, PH_H_F64);
-    apply_mdagm(c, HDCG_F64, xhi, r64, nullptr, -1.0, 1.0, b64);
+    residual_df(c, 1, b64, xhi, r64);
   }
   if (st) ++st->n_mdagm_f64;
   norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR));
@@ -414,7 +427,7 @@ static void true_residual_multi(Ctx& c, int op, int R, const uint4* b64, const u
   uint4* r64 = c.scratch(HDCG_F64, SL_R64, R);
   {
     PhaseTimer pt(c, PH_H_F64);
-    apply_mdagm_multi(c, HDCG_F64, R, xhi, r64, nullptr, -1.0, 1.0, b64);
+    residual_df(c, R, b64, xhi, r64);
   }
   if (st) st->n_mdagm_f64 += R;
   norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR), R);

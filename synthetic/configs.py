@@ -69,4 +69,10 @@ WORKLOADS = {
     "cfg5_32x32x32x64_ls16_mobius_3lvl": Workload(
         "cfg5_32x32x32x64_ls16_mobius_3lvl", (32, 32, 32, 64), 16, 1.8, 1.5, 0.5, 0.001, 0.45,
         (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=5),
+    # Profiling case for the coarse level: the 24^3 x 48 coarse grid and Nvec of
+    # cfg3 (an 860 MB FP16 little Dirac operator, larger than L2) over Ls = 2,
+    # so the fine subspace stays near 1 GB.
+    "prof_coarse_24x24x24x48_ls2": Workload(
+        "prof_coarse_24x24x24x48_ls2", (24, 24, 24, 48), 2, 1.8, 1.5, 0.5, 0.002, 0.4,
+        (4, 4, 4, 4), 32, 1e-8, "f16", seed=6),
 }

@@ -15,7 +15,8 @@ def torch_or_skip():
 def to_gpu(x, prec):
     """complex128 numpy array -> contiguous CUDA tensor of interleaved reals in the ABI precision."""
     import torch
-    dt = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16, 4: torch.bfloat16}[prec]
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16, 4: torch.bfloat16,
+          5: torch.float64}[prec]
     r = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)))
     if prec == 4:
         # truncation of the float32 word: keep its top 16 bits

@@ -1,6 +1,8 @@
 """Parity of the CUDA fine operator (through the C ABI) with the FP64 oracle.
 
-Tolerances (relative L2 over the whole output): FP64 1e-12; FP32 1e-6 and
+Tolerances (relative L2 over the whole output): FP64 1e-12, and 1e-12 too for
+the double-float operator (about 48 significant bits, 2^-48 ~ 3.6e-15 per
+rounding); FP32 1e-6 and
 FP16 storage 3e-3 (the operator-apply bars of the specification); BF16 with
 round-to-nearest 2e-2 and with truncation 4e-2 (8-bit mantissa: ~4e-3 per
 rounding, about eight roundings of input, links and intermediates).
@@ -10,12 +12,12 @@ import pytest
 
 import synthetic as sy
 from oracle.dwf import DWF, norm2
-from paper_1402_2585_gb300 import BF16, BF16T, F16, F32, F64, Hdcg, HdcgError
+from paper_1402_2585_gb300 import BF16, BF16T, DF64, F16, F32, F64, Hdcg, HdcgError
 from tests.gpu_util import from_gpu, rel, to_gpu, torch_or_skip
 
 pytestmark = pytest.mark.gpu
 
-TOL = {F64: 1e-12, F32: 1e-6, F16: 3e-3, BF16: 2e-2, BF16T: 4e-2}
+TOL = {F64: 1e-12, DF64: 1e-12, F32: 1e-6, F16: 3e-3, BF16: 2e-2, BF16T: 4e-2}
 
 CASES = {
     "shamir_4x4x4x4_ls4": dict(dims=(4, 4, 4, 4), Ls=4, b=1.0, c=0.0, m=0.01, eps=0.3, apbc=False),
@@ -38,7 +40,7 @@ def _setup(case, seed=0):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("prec", [F64, F32, F16, BF16, BF16T])
+@pytest.mark.parametrize("prec", [F64, DF64, F32, F16, BF16, BF16T])
 def test_mpc_and_mdagm_parity(case, prec):
     torch, d, h = _setup(case)
     psi = sy.gaussian_fermion(d.lat.dims, d.Ls, 600)
@@ -55,8 +57,10 @@ def test_mpc_and_mdagm_parity(case, prec):
     assert pHp == pytest.approx(norm2(d.mpc(psi)), rel=max(TOL[prec], 1e-12))
 
 
-def test_mdagm_full_size_fp32_16x16x16x16_ls16():
-    """The two-level workload's lattice (16^4 x 16, Shamir, m = 0.005) in FP32."""
+@pytest.mark.parametrize("prec", [F32, DF64])
+def test_mdagm_full_size_16x16x16x16_ls16(prec):
+    """The two-level workload's lattice (16^4 x 16, Shamir, m = 0.005) in FP32
+    (the outer operator) and double-float (the true-residual operator)."""
     w = sy.WORKLOADS["cfg2_16x16x16x16_ls16_shamir"]
     torch = torch_or_skip()
     U = sy.gauge_field(w.dims, w.eps, w.gauge_seed)
@@ -65,10 +69,10 @@ def test_mdagm_full_size_fp32_16x16x16x16_ls16():
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(U).cuda())
     psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
-    x = to_gpu(psi, F32)
+    x = to_gpu(psi, prec)
     y = torch.empty_like(x)
-    h.apply_mdagm(x, y, prec=F32)
-    assert rel(from_gpu(y), d.mdagm(psi)) < 1e-6
+    h.apply_mdagm(x, y, prec=prec)
+    assert rel(from_gpu(y), d.mdagm(psi)) < TOL[prec]
 
 
 def test_deterministic_and_hermitian():
