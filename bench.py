@@ -156,7 +156,7 @@ def run_ours(args, w):
     import torch
     import torch.distributed as dist
 
-    from paper_1402_2585_gb300 import ALG_ADEF2, ALG_CG, F64, Hdcg
+    from paper_1402_2585_gb300 import ALG_ADEF2, ALG_CG, F64, Hdcg, HdcgError
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -195,13 +195,15 @@ def run_ours(args, w):
         h.build_coarse_deflation(args.ldop_nvec, inv_steps=args.ldop_steps, shift=args.ldop_shift,
                                  tol=args.ldop_tol, maxiter=20000, seed=w.subspace_seed + 7 + rank)
         lam = h.get_coarse_deflation(args.ldop_nvec)
+        fin = lam[np.isfinite(lam)]
         ldop = {"nvec": args.ldop_nvec, "inv_steps": args.ldop_steps, "shift": args.ldop_shift,
-                "tol": args.ldop_tol, "ritz_min": float(lam[0]), "ritz_max": float(lam[-1])}
+                "tol": args.ldop_tol, "dropped": int(len(lam) - len(fin)),
+                "ritz_min": float(fin[0]) if len(fin) else None, "ritz_max": float(fin[-1]) if len(fin) else None}
     t_ldop = time.perf_counter() - t_l0
     setup_s = time.perf_counter() - t_setup0
 
     outer = 0 if prec == 0 else 1
-    nrhs = w.nrhs
+    nrhs = args.nrhs or w.nrhs
     prm = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000,
                               reliable_delta=args.reliable_delta, batch=1)
     prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000,
@@ -213,8 +215,14 @@ def run_ours(args, w):
     x = torch.zeros_like(b)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    for _ in range(args.warmup):
-        h.solve(b, x, w.tol, prm, nrhs=nrhs)
+    try:
+        for _ in range(args.warmup):
+            h.solve(b, x, w.tol, prm, nrhs=nrhs)
+    except HdcgError as e:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": str(e), "workload": w.name, "ldop_deflation": ldop,
+                              "coarse_storage": args.coarse_prec}), flush=True)
+        raise
     barrier()
 
     clk = ClockSampler(local)
@@ -354,13 +362,13 @@ def run_apply_only(args, w):
     import torch
 
     from paper_1402_2585_gb300 import Hdcg
-    prec = PREC[w.prec]
+    prec = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 5}[args.apply_prec] if args.apply_prec else PREC[w.prec]
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(sy.gauge_field(w.dims, w.eps, w.gauge_seed)).to(dev))
-    dt = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}[prec]
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16, 5: torch.float64}[prec]
     psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
     x = torch.view_as_real(torch.from_numpy(psi)).to(dt).to(dev).contiguous()
     y = torch.empty_like(x)
@@ -376,7 +384,7 @@ def run_apply_only(args, w):
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
-    print(json.dumps({"workload": w.name, "applies": args.apply_only,
+    print(json.dumps({"workload": w.name, "applies": args.apply_only, "prec": prec,
                       "ms_per_apply": e0.elapsed_time(e1) / args.apply_only}), flush=True)
 
 
@@ -443,6 +451,8 @@ def main():
     ap.add_argument("--reliable-delta", type=float, default=0.01, help="FP64 true-residual update factor")
     ap.add_argument("--coarse-prec", choices=["f64", "f32", "f16"], default=None,
                     help="storage of the little Dirac operator (default: the workload's)")
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="right-hand sides per solve (default: the workload's; reported as rhs_per_gpu)")
     ap.add_argument("--ldop-nvec", type=int, default=0,
                     help="second-level deflation vectors of the little Dirac operator (0: none)")
     ap.add_argument("--ldop-steps", type=int, default=3, help="inverse-iteration steps of that space")
@@ -451,6 +461,8 @@ def main():
     ap.add_argument("--ldop-tol", type=float, default=1e-5, help="coarse CG residual of those steps")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling case: run this many H applies only (no solve)")
+    ap.add_argument("--apply-prec", choices=["f64", "f32", "f16", "bf16", "df64"], default=None,
+                    help="with --apply-only: operator precision (default: the workload's storage)")
     ap.add_argument("--coarse-rhs", type=int, default=0,
                     help="with --coarse-only: apply to this many right-hand sides at once (hdcg_coarse_apply_multi)")
     ap.add_argument("--coarse-only", type=int, default=0,

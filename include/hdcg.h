@@ -223,7 +223,10 @@ typedef struct {
 int hdcg_build_coarse_deflation(hdcg_t h, const hdcg_ldop_params* p);
 
 /* The Ritz values lam (nvec doubles, ascending; host) and optionally the
- * vectors Z (canonical complex double [nvec][Vc][Nvec], host; may be NULL). */
+ * vectors Z (canonical complex double [nvec][Vc][Nvec], host; may be NULL).
+ * Pairs with lam <= 1e-7 lam_max (the computed operator need not be positive
+ * definite at the bottom of its spectrum at light masses) are left out of the
+ * deflation and reported as lam = +inf. */
 int hdcg_get_coarse_deflation(hdcg_t h, double* lam_host, void* Z_host);
 
 /* ---------------------------------------------------------------------------

@@ -595,6 +595,8 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   A.tc_choice = -1;
   A.defl.nd = 0;            // a deflation space belongs to the operator it was built for
   A.defl.lam_h.clear();
+  A.graph_cg.reset();
+  A.graph_ad1.reset();
   A.nvec = s.nvec;
   A.Vc = s.Vc;
   std::vector<int> nb(s.Vc * 81);
@@ -1161,7 +1163,7 @@ static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol
   return h.iter;
 }
 
-// Single right-hand side with an FP16 operator: time eight iterations of the
+// Single right-hand side with an FP16/FP32 operator: time eight iterations of the
 // CUDA-core and of the tensor-core coarse CG once per operator, keep the faster.
 static void tune_single(Ctx& c, Coarse& A, const void* rhs, void* sol) {
   coarse_tc_prepare(c, A);
@@ -1173,10 +1175,14 @@ static void tune_single(Ctx& c, Coarse& A, const void* rhs, void* sol) {
   cudaEvent_t e[3];
   for (auto& ev : e) HDCG_CUDA(cudaEventCreate(&ev));
   A.last_iters = 8;
-  coarse_cg_t<__half2, float>(c, A, rhs, sol, 1e-30, 8);
+  auto core = [&] {
+    if (A.prec == HDCG_F32) coarse_cg_t<float2, float>(c, A, rhs, sol, 1e-30, 8);
+    else coarse_cg_t<__half2, float>(c, A, rhs, sol, 1e-30, 8);
+  };
+  core();
   coarse_cg_tc(c, A, 1, rhs, sol, 1e-30, 8);
   HDCG_CUDA(cudaEventRecord(e[0], c.stream));
-  coarse_cg_t<__half2, float>(c, A, rhs, sol, 1e-30, 8);
+  core();
   HDCG_CUDA(cudaEventRecord(e[1], c.stream));
   coarse_cg_tc(c, A, 1, rhs, sol, 1e-30, 8);
   HDCG_CUDA(cudaEventRecord(e[2], c.stream));

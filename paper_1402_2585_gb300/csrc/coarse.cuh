@@ -34,8 +34,9 @@ struct Coarse {
   int last_iters = 8;
   // tensor-core form (FP16 A only): A re-tiled for tcgen05, the B tiles of the
   // current vectors, and a small state block (wait-timeout flags, per-rhs max|x|)
-  DevMem Atc, xtc, tcs;
+  DevMem Atc, xtc, tcs, sexp;
   bool tc_ready = false;
+  CapturedGraph graph_cg, graph_ad1;   // captured iteration pairs of the coarse solvers
   int tc_choice = -1;       // single right-hand side: -1 undecided, 0 CUDA cores, 1 tensor cores
   // second-level (global) deflation space of A, prediagonalised: Z^dag A Z = diag(lam)
   struct Defl {
@@ -43,7 +44,8 @@ struct Coarse {
     DevMem Z;               // [nd][Vc*Nvec] complex float
     DevMem W;               // [nd][Vc*Nvec] complex float: Z - A Z
     DevMem lam;             // [nd] double
-    std::vector<double> lam_h;
+    std::vector<double> lam_h;   // +inf marks a pair dropped from Q (non-positive or ~0)
+    int dropped = 0;
   } defl;
   int vec_prec() const { return prec == HDCG_F64 ? HDCG_F64 : HDCG_F32; }
   size_t vec_bytes() const { return Vc * nvec * (vec_prec() == HDCG_F64 ? 16 : 8); }
@@ -56,10 +58,10 @@ struct TcState {
   unsigned xmax[RMAX];      // per right-hand side max(|Re x|, |Im x|) as float bits
 };
 struct TcGeom {
-  int sites, MS, Kp, Rp, NS, NMMA, ncols, stages;
-  uint32_t a_bytes, b_bytes, stage_bytes;
+  int sites, MS, Kp, Rp, NS, NMMA, ncols, stages, parts;
+  uint32_t a_bytes, b_bytes, stage_bytes;   // a_bytes: one FP16 part of one block
 };
-TcGeom tc_geom(int nvec, int R);
+TcGeom tc_geom(int nvec, int R, int parts);
 bool coarse_tc_supported(const Coarse& A);
 void coarse_tc_prepare(Ctx& c, Coarse& A);
 // coarse CG on R right-hand sides (FP32 vectors [a][k][r]) with the tensor-core operator

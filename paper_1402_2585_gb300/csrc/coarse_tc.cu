@@ -14,6 +14,12 @@
 // Re X_hi] + D[., Re X_lo] and Q = D[., Im X_hi] + D[., Im X_lo] of the two
 // rows of coefficient j (adjacent TMEM lanes, exchanged by one shuffle).
 //
+// Every coarse site's 81 blocks carry one power-of-two scale (largest entry in
+// [2^13, 2^14)), so the far couplings, many orders of magnitude below the
+// diagonal block, stay in FP16's normal range; the epilogue removes it.  An FP32
+// operator is split into FP16 hi + lo parts (about 22 significant bits) that
+// enter as two MMAs against the same B tile; an FP16 operator is one part.
+//
 // With Nvec <= 32 a block has 2 Nvec <= 64 rows, so two coarse sites share
 // one M = 128 MMA (rows 0..63 site a0, 64..127 site a1) against B = [B_{a0+l}
 // | B_{a1+l}]; the two off-diagonal quadrants of D are discarded.  With
@@ -29,6 +35,7 @@
 // warps 2..5 read the accumulator (one TMEM lane quarter each), combine,
 // unscale and store Y and the per-right-hand-side <X, Y>.
 #include <algorithm>
+#include <cstring>
 
 #include "coarse.cuh"
 #include "tc.cuh"
@@ -65,7 +72,7 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) 
 
 }  // namespace
 
-TcGeom tc_geom(int nvec, int R) {
+TcGeom tc_geom(int nvec, int R, int parts) {
   HDCG_REQUIRE(nvec >= 1 && nvec <= 64, HDCG_ERR_ARG, "tensor-core coarse operator needs Nvec <= 64");
   HDCG_REQUIRE(R >= 1 && R <= TC_RPMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   TcGeom g;
@@ -80,16 +87,43 @@ TcGeom tc_geom(int nvec, int R) {
   while (g.ncols < g.NMMA) g.ncols *= 2;
   g.a_bytes = (uint32_t)g.MS * g.Kp * 2;
   g.b_bytes = (uint32_t)g.NS * g.Kp * 2;
-  g.stage_bytes = g.sites * (g.a_bytes + g.b_bytes);
+  g.parts = parts;
+  g.stage_bytes = g.sites * (parts * g.a_bytes + g.b_bytes);
   g.stages = (int)std::min<uint32_t>(16, TC_RING_BYTES / g.stage_bytes);
   g.stages = std::max(g.stages, 2);
   return g;
 }
 
-// A (FP16, [a][l][k][j] half2) -> tiled operand, one 16-byte row segment per thread:
-// element (m, k) of block (a, l) at byte (m/8)(16 Kp) + (k/8) 128 + (m%8) 16 + (k%8) 2.
-__global__ void k_a_to_tc(const __half2* __restrict__ A, uint4* __restrict__ Atc, size_t nblk, int n, int MS,
-                          int Kp) {
+__device__ __forceinline__ float2 a_value(const __half2* A, size_t i) { return __half22float2(A[i]); }
+__device__ __forceinline__ float2 a_value(const float2* A, size_t i) { return A[i]; }
+
+// per coarse site: scale exponent bringing the largest |Re|, |Im| of its 81 blocks into [2^13, 2^14)
+template <typename AT>
+__global__ void k_site_scale(const AT* __restrict__ A, int n, int* sexp) {
+  const size_t a = blockIdx.x;
+  const size_t per = (size_t)81 * n * n;
+  float m = 0.f;
+  for (size_t i = threadIdx.x; i < per; i += blockDim.x) {
+    const float2 v = a_value(A, a * per + i);
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  __shared__ float sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
+    sexp[a] = scale_exp(__float_as_uint(fmaxf(m, sm[0])));
+  }
+}
+
+// A ([a][l][k][j] complex, FP16 or FP32) -> tiled operand, one 16-byte row segment per
+// thread: element (m, k) of part p of block (a, l) at byte p a_bytes + (m/8)(16 Kp) +
+// (k/8) 128 + (m%8) 16 + (k%8) 2, a_bytes = MS Kp 2; part 0 = hi, part 1 = lo.
+template <typename AT>
+__global__ void k_a_to_tc(const AT* __restrict__ A, uint4* __restrict__ Atc, size_t nblk, int n, int MS, int Kp,
+                          int parts, const int* __restrict__ sexp) {
   const int KG = Kp / 8;
   const size_t per = (size_t)MS * KG;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,20 +132,25 @@ __global__ void k_a_to_tc(const __half2* __restrict__ A, uint4* __restrict__ Atc
   const int rem = (int)(t % per);
   const int m = rem / KG, kg = rem % KG;
   const int j = m >> 1, ri = m & 1;
-  __align__(16) __half v[8];
+  const float s = pow2f(sexp[blk / 81]);
+  __align__(16) __half hi[8];
+  __align__(16) __half lo[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int k = kg * 8 + q;
-    __half h = __float2half_rn(0.f);
+    float x = 0.f;
     if (j < n && k < n) {
-      const __half2 e = A[(blk * n + k) * n + j];
-      h = ri ? __high2half(e) : __low2half(e);
+      const float2 e = a_value(A, (blk * n + k) * n + j);
+      x = (ri ? e.y : e.x) * s;
     }
-    v[q] = h;
+    hi[q] = __float2half_rn(x);
+    lo[q] = __float2half_rn(x - __half2float(hi[q]));
   }
-  char* dst = reinterpret_cast<char*>(Atc) + blk * (size_t)MS * Kp * 2 + (size_t)(m / 8) * (Kp * 16) + kg * 128 +
+  const size_t a_bytes = (size_t)MS * Kp * 2;
+  char* dst = reinterpret_cast<char*>(Atc) + blk * parts * a_bytes + (size_t)(m / 8) * (Kp * 16) + kg * 128 +
               (m % 8) * 16;
-  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(hi);
+  if (parts == 2) *reinterpret_cast<uint4*>(dst + a_bytes) = *reinterpret_cast<const uint4*>(lo);
 }
 
 // X (FP32 complex [a][k][r]) -> tiled B operand of every coarse site: thread
@@ -185,13 +224,15 @@ struct TcArgs {
   int Vc, n, R, sites, MS, Kp, NS, stages, ncols;
   uint32_t a_bytes, b_bytes, idesc;
   float shift;         // Y = (A + shift) X (needs x)
+  int parts;           // 1: FP16 operator, 2: FP32 operator as FP16 hi + lo
+  const int* sexp;     // per-site scale exponents of the tiled operator
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction red) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (g.skip && *g.skip) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t stage_bytes = g.sites * (g.a_bytes + g.b_bytes);
+  const uint32_t stage_bytes = g.sites * (g.parts * g.a_bytes + g.b_bytes);
   const uint32_t ring = tc::smem_u32(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * stage_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * g.stages + 3);
@@ -240,14 +281,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
           }
           tc::mbar_arrive_expect_tx(TC_FULL(s), stage_bytes);
           const uint32_t dst = ring + (uint32_t)s * stage_bytes;
-          for (int si = 0; si < g.sites; ++si) {
-            const size_t blk = (size_t)site[si] * 81 + l;
-            tc::bulk_g2s(dst + si * g.a_bytes, reinterpret_cast<const char*>(g.Atc) + blk * g.a_bytes, g.a_bytes,
-                         TC_FULL(s));
-          }
+          // stage: [part 0: site 0, site 1][part 1: site 0, site 1][B site 0][B site 1]
+          for (int p = 0; p < g.parts; ++p)
+            for (int si = 0; si < g.sites; ++si) {
+              const size_t blk = (size_t)site[si] * 81 + l;
+              tc::bulk_g2s(dst + (p * g.sites + si) * g.a_bytes,
+                           reinterpret_cast<const char*>(g.Atc) + (blk * g.parts + p) * g.a_bytes, g.a_bytes,
+                           TC_FULL(s));
+            }
           for (int si = 0; si < g.sites; ++si) {
             const int nb = __ldg(g.cnbr + (size_t)site[si] * 81 + l);
-            tc::bulk_g2s(dst + g.sites * g.a_bytes + si * g.b_bytes,
+            tc::bulk_g2s(dst + g.sites * g.parts * g.a_bytes + si * g.b_bytes,
                          reinterpret_cast<const char*>(g.xtc) + (size_t)nb * g.b_bytes, g.b_bytes, TC_FULL(s));
           }
         }
@@ -281,11 +325,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
           }
           tc::fence_after_sync();
           const uint32_t abase = ring + (uint32_t)s * stage_bytes;
-          const uint32_t bbase = abase + g.sites * g.a_bytes;
+          const uint32_t bbase = abase + g.sites * g.parts * g.a_bytes;
           for (int ks = 0; ks < g.Kp / 16; ++ks) {
-            const uint64_t ad = tc::smem_desc(abase + 256u * ks, 128u, sbo);
             const uint64_t bd = tc::smem_desc(bbase + 256u * ks, 128u, sbo);
-            tc::mma_f16(tmem, ad, bd, g.idesc, (l | ks) != 0 ? 1u : 0u);
+            for (int p = 0; p < g.parts; ++p) {
+              const uint64_t ad = tc::smem_desc(abase + p * g.sites * g.a_bytes + 256u * ks, 128u, sbo);
+              tc::mma_f16(tmem, ad, bd, g.idesc, (l | ks | p) != 0 ? 1u : 0u);
+            }
           }
           tc::mma_commit(TC_EMPTY(s));
         }
@@ -322,13 +368,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
       if (lane == 0) tc::mbar_arrive(ACC_EMPTY);
       const int site = p * g.sites + si;
       const bool valid = site < g.Vc && j < g.n;
+      const float sinv = valid ? pow2f(-__ldg(g.sexp + site)) : 0.f;
 #pragma unroll
       for (int r = 0; r < TC_RPMAX; ++r) {
         if (r < g.R) {
           const float P = d[4 * r] + d[4 * r + 2];
           const float Q = d[4 * r + 1] + d[4 * r + 3];
           const float t = __shfl_xor_sync(FULL_MASK, Q, 1);
-          float v = (ri ? t + P : P - t) * inv[r];
+          float v = (ri ? t + P : P - t) * (inv[r] * sinv);
           if (valid) {
             const size_t e = ((size_t)site * g.n + j) * g.R + r;
             if (g.x) {
@@ -356,21 +403,35 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
 // host side
 // ---------------------------------------------------------------------------------
 
-bool coarse_tc_supported(const Coarse& A) { return A.prec == HDCG_F16 && A.nvec >= 1 && A.nvec <= 64; }
+bool coarse_tc_supported(const Coarse& A) {
+  return (A.prec == HDCG_F16 || A.prec == HDCG_F32) && A.nvec >= 1 && A.nvec <= 64;
+}
+static int tc_parts(const Coarse& A) { return A.prec == HDCG_F32 ? 2 : 1; }
 
 void coarse_tc_prepare(Ctx& c, Coarse& A) {
-  HDCG_REQUIRE(coarse_tc_supported(A), HDCG_ERR_ARG, "tensor-core coarse operator needs FP16 A and Nvec <= 64");
+  HDCG_REQUIRE(coarse_tc_supported(A), HDCG_ERR_ARG,
+               "tensor-core coarse operator needs an FP16 or FP32 A and Nvec <= 64");
   if (A.tc_ready) return;
-  const TcGeom g = tc_geom(A.nvec, 1);
+  const int parts = tc_parts(A);
+  const TcGeom g = tc_geom(A.nvec, 1, parts);
   const size_t nblk = A.Vc * 81;
-  A.Atc.ensure(nblk * g.a_bytes);
+  A.Atc.ensure(nblk * parts * g.a_bytes);
+  A.sexp.ensure(A.Vc * sizeof(int));
   A.tcs.ensure(sizeof(TcState));
   HDCG_CUDA(cudaMemsetAsync(A.tcs.p, 0, sizeof(TcState), c.stream));
   const size_t nt = nblk * g.MS * (g.Kp / 8);
-  k_a_to_tc<<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(A.A.as<__half2>(), A.Atc.as<uint4>(), nblk,
-                                                                 A.nvec, g.MS, g.Kp);
+  if (A.prec == HDCG_F32) {
+    k_site_scale<float2><<<(unsigned)A.Vc, 256, 0, c.stream>>>(A.A.as<float2>(), A.nvec, A.sexp.as<int>());
+    k_a_to_tc<float2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(A.A.as<float2>(), A.Atc.as<uint4>(), nblk,
+                                                                          A.nvec, g.MS, g.Kp, parts, A.sexp.as<int>());
+  } else {
+    k_site_scale<__half2><<<(unsigned)A.Vc, 256, 0, c.stream>>>(A.A.as<__half2>(), A.nvec, A.sexp.as<int>());
+    k_a_to_tc<__half2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(A.A.as<__half2>(), A.Atc.as<uint4>(),
+                                                                           nblk, A.nvec, g.MS, g.Kp, parts,
+                                                                           A.sexp.as<int>());
+  }
   HDCG_CUDA(cudaGetLastError());
-  ++c.launches;
+  c.launches += 2;
   A.tc_ready = true;
 }
 
@@ -393,7 +454,7 @@ void coarse_tc_max(Ctx& c, const float2* x, size_t ne, int R, unsigned* xmax) {
 }
 
 void coarse_tc_to_b(Ctx& c, Coarse& A, int R, const float2* x, const unsigned* xmax, const int* skip) {
-  const TcGeom g = tc_geom(A.nvec, R);
+  const TcGeom g = tc_geom(A.nvec, R, tc_parts(A));
   A.xtc.ensure(A.Vc * (size_t)g.b_bytes);
   const size_t nt = A.Vc * (size_t)(g.Kp / 8) * g.Rp;
   k_x_to_tc<<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(x, A.xtc.as<uint4>(), A.Vc, A.nvec, R, g.Rp, g.Kp,
@@ -404,7 +465,7 @@ void coarse_tc_to_b(Ctx& c, Coarse& A, int R, const float2* x, const unsigned* x
 
 void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
                      double* dot_result, double shift) {
-  const TcGeom g = tc_geom(A.nvec, R);
+  const TcGeom g = tc_geom(A.nvec, R, tc_parts(A));
   TcArgs a;
   a.Atc = A.Atc.as<uint4>();
   a.cnbr = A.cnbr.as<int>();
@@ -427,6 +488,8 @@ void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const
   a.b_bytes = g.b_bytes;
   a.idesc = tc::idesc_f16_f32(128, g.NMMA);
   a.shift = (float)shift;
+  a.parts = g.parts;
+  a.sexp = A.sexp.as<int>();
   const size_t smem = (size_t)g.stages * g.stage_bytes + (2 * g.stages + 3) * 8 + 16;
   static size_t smem_set = 0;
   if (smem > smem_set) {
@@ -600,19 +663,36 @@ int coarse_cg_tc(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
                                        make_reduction(c, ge, RMAX, &ctl->rr[0][0], 0));
   k_cgt_start<<<1, 1, 0, c.stream>>>(ctl, R, tol, maxiter);
   c.launches += 2;
+  auto iteration = [&](int par) {
+    coarse_tc_to_b(c, A, R, p, xmax, skip);
+    coarse_tc_apply(c, A, R, p, w, xmax, skip, &ctl->pAp[0], shift);
+    k_cgt_update<<<ge, 256, 0, c.stream>>>((float2*)sol, r, p, w, ne, R, ctl, par, xmax,
+                                           make_reduction(c, ge, RMAX, &ctl->rr[par ^ 1][0], 0));
+    k_cgt_p<<<ge, 256, 0, c.stream>>>(p, r, ne, R, ctl, par, xmax);
+    k_cgt_check<<<1, 1, 0, c.stream>>>(ctl, R, par, maxiter);
+    c.launches += 3;
+  };
+  // pairs of iterations (parities 0, 1): the first directly, later ones as a replayed graph
+  uint64_t shift_bits;
+  std::memcpy(&shift_bits, &shift, sizeof(shift_bits));
+  const std::vector<uintptr_t> key = {(uintptr_t)A.work.p, (uintptr_t)A.ctl.p, (uintptr_t)sol, (uintptr_t)A.Atc.p,
+                                      (uintptr_t)A.xtc.p, (uintptr_t)A.tcs.p, (uintptr_t)c.red_partials.p,
+                                      (uintptr_t)c.red_ticket.p, (uintptr_t)R, (uintptr_t)maxiter,
+                                      (uintptr_t)shift_bits};
   int queued = 0;
-  int batch = std::max(1, A.last_iters);
+  int batch = std::max(2, A.last_iters);
   CCtlT h{};
   while (true) {
-    for (int bq = 0; bq < batch && queued < maxiter; ++bq, ++queued) {
-      const int par = queued & 1;
-      coarse_tc_to_b(c, A, R, p, xmax, skip);
-      coarse_tc_apply(c, A, R, p, w, xmax, skip, &ctl->pAp[0], shift);
-      k_cgt_update<<<ge, 256, 0, c.stream>>>((float2*)sol, r, p, w, ne, R, ctl, par, xmax,
-                                             make_reduction(c, ge, RMAX, &ctl->rr[par ^ 1][0], 0));
-      k_cgt_p<<<ge, 256, 0, c.stream>>>(p, r, ne, R, ctl, par, xmax);
-      k_cgt_check<<<1, 1, 0, c.stream>>>(ctl, R, par, maxiter);
-      c.launches += 3;
+    for (int bq = 0; bq < batch && queued < maxiter; bq += 2, queued += 2) {
+      if (queued == 0) {
+        iteration(0);
+        iteration(1);
+      } else {
+        run_captured(c, A.graph_cg, key, [&] {
+          iteration(0);
+          iteration(1);
+        });
+      }
     }
     HDCG_CUDA(cudaGetLastError());
     HDCG_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(CCtlT), cudaMemcpyDeviceToHost, c.stream));
@@ -678,7 +758,7 @@ void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   const size_t ne = A.Vc * A.nvec, nc = ne * R;
   const unsigned gt = (unsigned)((nc + 255) / 256);
-  if (A.prec == HDCG_F16) {
+  if (coarse_tc_supported(A)) {
     coarse_tc_prepare(c, A);
     DevMem tmp;
     tmp.ensure(2 * nc * sizeof(float2));

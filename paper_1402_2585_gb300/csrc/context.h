@@ -196,6 +196,58 @@ void norm2(Ctx& c, const uint4* a, int prec, size_t n_reals, double* result, int
 // result[0:2] = <a, b> (complex)
 void cdot(Ctx& c, const uint4* a, const uint4* b, int prec, size_t n_reals, double* result);
 
+// A launch sequence captured once from the handle's stream and replayed as one
+// CUDA graph (the launch-bound inner loops of the coarse solvers).  The key
+// lists every buffer and scalar baked into the captured launches; a different
+// key captures again.  Graphs are not used on the legacy default stream or
+// while the caller is itself capturing that stream.
+struct CapturedGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;
+  long long launches = 0;   // kernels per replay (added to the handle's count)
+  CapturedGraph() = default;
+  CapturedGraph(const CapturedGraph&) = delete;
+  CapturedGraph& operator=(const CapturedGraph&) = delete;
+  ~CapturedGraph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key.clear();
+  }
+};
+
+template <typename F>
+void run_captured(Ctx& c, CapturedGraph& g, const std::vector<uintptr_t>& key, F&& body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (c.stream == nullptr || cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    body();
+    return;
+  }
+  if (!g.exec || g.key != key) {
+    g.reset();
+    const long long l0 = c.launches;
+    cudaGraph_t graph = nullptr;
+    HDCG_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(c.stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    HDCG_CUDA(cudaStreamEndCapture(c.stream, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HDCG_CUDA(e);
+    g.key = key;
+    g.launches = c.launches - l0;
+    c.launches = l0;
+  }
+  HDCG_CUDA(cudaGraphLaunch(g.exec, c.stream));
+  c.launches += g.launches;
+}
+
 // RAII phase timer: records (start, stop) events when profiling is on
 struct PhaseTimer {
   Ctx& c;

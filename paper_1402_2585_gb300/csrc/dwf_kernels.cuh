@@ -117,45 +117,40 @@ __device__ __forceinline__ void load_link(const __nv_bfloat162*, const uint4* __
 // shift (psi_{s-1}) and on chirality - as the up shift (psi_{s+1}); P_s^dag
 // swaps them.  Wrapped values pick up -m.
 // ------------------------------------------------------------------------------
-template <typename R, bool DAG>
-__device__ __forceinline__ void apply_Ppow(R* v, int d, int s, int Ls, R m) {
-  const int up_src = (s + d) & (Ls - 1);
-  const R up_f = (s + d >= Ls) ? -m : R(1);
-  const int dn_src = (s - d) & (Ls - 1);
-  const R dn_f = (s < d) ? -m : R(1);
-  const int sp = DAG ? up_src : dn_src;
-  const R fp = DAG ? up_f : dn_f;
-  const int sm = DAG ? dn_src : up_src;
-  const R fm = DAG ? dn_f : up_f;
-#pragma unroll
-  for (int i = 0; i < 12; ++i) v[i] = fp * shfl_any(v[i], sp, Ls);
-#pragma unroll
-  for (int i = 12; i < 24; ++i) v[i] = fm * shfl_any(v[i], sm, Ls);
-}
+// Each element shuffles only itself, so the shift-and-combine steps below
+// update v in place (every lane reads its source lane's old value in the same
+// warp-wide shuffle) with the wall factor folded into one coefficient per
+// chirality: one shuffle and one multiply-add per real.
 
 // v <- a v + b P v
 template <typename R, bool DAG>
 __device__ __forceinline__ void apply_lin(R* v, R a, R b, int s, int Ls, R m) {
-  R t[24];
+  const int up_src = (s + 1) & (Ls - 1), dn_src = (s - 1) & (Ls - 1);
+  const R up_f = (s + 1 >= Ls) ? -m : R(1), dn_f = (s < 1) ? -m : R(1);
+  const int sp = DAG ? up_src : dn_src, sm = DAG ? dn_src : up_src;
+  const R bp = b * (DAG ? up_f : dn_f), bm = b * (DAG ? dn_f : up_f);
 #pragma unroll
-  for (int i = 0; i < 24; ++i) t[i] = v[i];
-  apply_Ppow<R, DAG>(t, 1, s, Ls, m);
+  for (int i = 0; i < 12; ++i) v[i] = a * v[i] + bp * shfl_any(v[i], sp, Ls);
 #pragma unroll
-  for (int i = 0; i < 24; ++i) v[i] = a * v[i] + b * t[i];
+  for (int i = 12; i < 24; ++i) v[i] = a * v[i] + bm * shfl_any(v[i], sm, Ls);
 }
 
 // v <- M_ee^-1 v (DAG: M_ee^-dag) by doubling: A_{j+1} = A_j + r^{2^j} P^{2^j} A_j
 template <typename R, bool DAG>
 __device__ __forceinline__ void apply_minv(R* v, int s, const HopArgs& a) {
   const R m = (R)a.mass;
+  const int Ls = a.Ls;
   for (int j = 0; j < a.lslog2; ++j) {
-    R t[24];
-#pragma unroll
-    for (int i = 0; i < 24; ++i) t[i] = v[i];
-    apply_Ppow<R, DAG>(t, 1 << j, s, a.Ls, m);
+    const int d = 1 << j;
+    const int up_src = (s + d) & (Ls - 1), dn_src = (s - d) & (Ls - 1);
+    const R up_f = (s + d >= Ls) ? -m : R(1), dn_f = (s < d) ? -m : R(1);
+    const int sp = DAG ? up_src : dn_src, sm = DAG ? dn_src : up_src;
     const R rp = (R)a.rpow[j];
+    const R cp = rp * (DAG ? up_f : dn_f), cm = rp * (DAG ? dn_f : up_f);
 #pragma unroll
-    for (int i = 0; i < 24; ++i) v[i] += rp * t[i];
+    for (int i = 0; i < 12; ++i) v[i] += cp * shfl_any(v[i], sp, Ls);
+#pragma unroll
+    for (int i = 12; i < 24; ++i) v[i] += cm * shfl_any(v[i], sm, Ls);
   }
   const R nrm = (R)a.minv_norm;
 #pragma unroll

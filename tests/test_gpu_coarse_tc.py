@@ -1,7 +1,8 @@
 """The little Dirac operator applied to several right-hand sides at once
-(hdcg_coarse_apply_multi): FP16 operators on the tensor cores (tcgen05),
-FP32/FP64 operators on the CUDA cores, against the FP64 oracle's stencil
-apply y_a = sum_l A[a][l] x_{a+delta_l} (Sec. 4.3).
+(hdcg_coarse_apply_multi): FP16 operators on the tensor cores (tcgen05), FP32
+operators on the tensor cores as FP16 hi + lo parts, FP64 operators on the
+CUDA cores, against the FP64 oracle's stencil apply
+y_a = sum_l A[a][l] x_{a+delta_l} (Sec. 4.3).
 
 The operator is a seeded random stencil rounded to the storage precision on
 the host (numpy) and uploaded with hdcg_set_coarse, so both sides apply the
@@ -104,12 +105,37 @@ def test_tensor_core_per_rhs_scaling():
 
 
 @pytest.mark.parametrize("prec,tol", [(F32, 1e-5), (F64, 1e-12)])
-def test_cuda_core_multi_apply(prec, tol):
+def test_fp32_split_and_fp64_multi_apply(prec, tol):
     torch, bl, h, A = _handle("full_12x12x12x12_ls2", 24, prec)
     X = sy.complex_normal(940, (5, bl.Vc, 24))
     Y = _multi(torch, h, X)
     for r in range(5):
         assert rel(Y[r], coarse_apply(A, X[r], bl)) < tol, f"rhs {r}"
+
+
+@pytest.mark.parametrize("R", [1, 16])
+def test_fp32_operator_with_hop_dependent_magnitudes(R):
+    """Couplings falling with the block hop distance like the paper's Table
+    frobnorm (627, 6.2, 0.08, 7e-4, 3e-5 for 0..4 hops): the per-site scale
+    keeps the small far blocks in FP16's normal range, and the hi + lo split
+    keeps the FP32 operator's accuracy.  x lives on one coarse site, so the
+    sites two or more hops away see only the small blocks; their error is
+    measured against the output's overall size (the operator's own scale)."""
+    torch, bl, h, A = _handle("full_12x12x12x12_ls2", 32, F32)
+    offs = np.array([[(l // 3 ** mu) % 3 - 1 for mu in range(4)] for l in range(81)])
+    hops = np.abs(offs).sum(axis=1)
+    frob = np.array([627.0, 6.2, 0.08, 7e-4, 3e-5])
+    A = (A * (frob[hops] / frob[0])[None, :, None, None]).astype(np.complex64).astype(np.complex128)
+    h.set_coarse(torch.from_numpy(A).cuda(), F32)
+    X = np.zeros((R, bl.Vc, 32), dtype=np.complex128)
+    X[:, 40] = sy.complex_normal(961, (R, 32))
+    Y = _multi(torch, h, X)
+    for r in range(R):
+        want = coarse_apply(A, X[r], bl)
+        assert rel(Y[r], want) < 1e-5
+        far = [a for a in range(bl.Vc) if np.abs(offs[a] - offs[40]).sum() >= 2]
+        err = np.abs(Y[r][far] - want[far]).max() / np.abs(want).max()
+        assert err < 1e-6, err
 
 
 @pytest.mark.parametrize("prec", [F16, F32, F64])
