@@ -35,6 +35,32 @@ DEFAULT_WORKLOAD = "cfg2_16x16x16x16_ls16_shamir"
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 
 
+# DRAM bytes (read + write) per FP32 hop_kernel launch, mean of the four passes of
+# one H, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the current kernel on this workload; to be reset to None whenever hop_kernel
+# changes, since the counters then no longer describe it.
+HOP_F32_TRAFFIC = {DEFAULT_WORKLOAD: 126.2e6}
+
+
+def replica_seeds(w, rank: int) -> dict:
+    """Seeds of rank `rank`'s replica: every rank solves its own independent
+    problem of the workload (weak scaling, no data-path collective); rank 0
+    uses the workload's own seeds."""
+    return {"gauge": w.gauge_seed + 100 * rank, "source": w.source_seed + rank,
+            "subspace": w.subspace_seed + rank, "ldop": w.subspace_seed + 7 + rank}
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest per-rank value: the job's time per step when every rank
+    solves its own replica (one all-reduce on the timing, outside the timed work)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -124,7 +150,7 @@ def cpu_sample_desc(w, n_h):
 # H applies per HDCG solve of the default workload, recorded from the GPU arm's
 # solve statistics (a property of the algorithm on this input); used only to
 # scale the oracle's per-apply time in --impl reference, which runs no GPU code.
-H_APPLIES_PER_SOLVE = {DEFAULT_WORKLOAD: 420}
+H_APPLIES_PER_SOLVE = {DEFAULT_WORKLOAD: 140}   # 15 outer + 120 preconditioner + 5 FP64 residual
 
 
 def run_reference(args, w):
@@ -133,7 +159,7 @@ def run_reference(args, w):
         return
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(k, "1")
-    n_h = H_APPLIES_PER_SOLVE.get(w.name, 420)
+    n_h = H_APPLIES_PER_SOLVE.get(w.name, 140)
     for _ in range(args.warmup):
         oracle_h_seconds(w)
     ts = [oracle_h_seconds(w) for _ in range(args.steps)]
@@ -176,13 +202,14 @@ def run_ours(args, w):
     sub_prec = prec if prec in (0, 1) else 2
     coarse_prec = 0 if prec == 0 else (1 if prec == 1 else 2)
     t_setup0 = time.perf_counter()
-    U = sy.gauge_field(w.dims, w.eps, w.gauge_seed + 100 * rank)
+    seeds = replica_seeds(w, rank)
+    U = sy.gauge_field(w.dims, w.eps, seeds["gauge"])
     h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(U).to(dev))
     t_sub0 = time.perf_counter()
     h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=args.inv_steps, inv_shift=0.0, inv_tol=args.inv_tol,
-                     inv_maxiter=20000, seed=w.subspace_seed + rank)
+                     inv_maxiter=20000, seed=seeds["subspace"])
     t_sub = time.perf_counter() - t_sub0
     t_c0 = time.perf_counter()
     if args.coarse_prec:
@@ -191,9 +218,11 @@ def run_ours(args, w):
     t_coarse = time.perf_counter() - t_c0
     t_l0 = time.perf_counter()
     ldop = None
+    if args.ldop_nvec is None:
+        args.ldop_nvec = w.ldop_nvec
     if args.ldop_nvec:
         h.build_coarse_deflation(args.ldop_nvec, inv_steps=args.ldop_steps, shift=args.ldop_shift,
-                                 tol=args.ldop_tol, maxiter=20000, seed=w.subspace_seed + 7 + rank)
+                                 tol=args.ldop_tol, maxiter=20000, seed=seeds["ldop"])
         lam = h.get_coarse_deflation(args.ldop_nvec)
         fin = lam[np.isfinite(lam)]
         ldop = {"nvec": args.ldop_nvec, "inv_steps": args.ldop_steps, "shift": args.ldop_shift,
@@ -209,7 +238,7 @@ def run_ours(args, w):
     prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000,
                                  reliable_delta=args.reliable_delta)
     if nrhs == 1:
-        b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, w.source_seed + rank)).to(dev)
+        b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, seeds["source"])).to(dev)
     else:
         b = torch.from_numpy(sy.point_sources(w.dims, w.Ls, nrhs)).to(dev)
     x = torch.zeros_like(b)
@@ -255,11 +284,7 @@ def run_ours(args, w):
     h.set_profiling(False)
     clocks = clk.stop()
 
-    t_local = statistics.mean(times)
-    t_all = torch.tensor([t_local], device=dev)
-    if world > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    t_solve = float(t_all.item())
+    t_solve = max_over_ranks(statistics.mean(times), world, dev)
 
     # plain red-black CG on the same GPU (same precision policy)
     cg_times, cg_stats = [], None
@@ -326,7 +351,8 @@ def run_ours(args, w):
                    "l2": "flushed (512 MiB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": HOP_F32_TRAFFIC.get(w.name) if outer == 1 else None,
                      "kernel": "hop_kernel (4 passes per H; FP32 storage)", "launches": n_hop,
                      "avg_launch_us": hop_ms * 1e3 / max(1, n_hop), "peak_kind": f"{peak_kind} HBM copy"},
         "cpu_baseline": cpu,
@@ -453,8 +479,9 @@ def main():
                     help="storage of the little Dirac operator (default: the workload's)")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="right-hand sides per solve (default: the workload's; reported as rhs_per_gpu)")
-    ap.add_argument("--ldop-nvec", type=int, default=0,
-                    help="second-level deflation vectors of the little Dirac operator (0: none)")
+    ap.add_argument("--ldop-nvec", type=int, default=None,
+                    help="second-level deflation vectors of the little Dirac operator (0: none; default: the "
+                         "workload's)")
     ap.add_argument("--ldop-steps", type=int, default=3, help="inverse-iteration steps of that space")
     ap.add_argument("--ldop-shift", type=float, default=-1e-3,
                     help="shift of those inverse-iteration steps (negative: times the mean diagonal of A)")

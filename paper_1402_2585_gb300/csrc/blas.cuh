@@ -7,6 +7,9 @@
 
 namespace hdcg {
 
+static_assert(RMAX == RED_RHS, "reduction groups hold one slot per right-hand side");
+
+
 // Run `body` with `T` bound to the storage tag of precision code `prec`.
 #define DISPATCH_PREC(prec, T, ...)                                   \
   switch (prec) {                                                     \

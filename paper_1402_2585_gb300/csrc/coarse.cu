@@ -1593,7 +1593,7 @@ __global__ void __launch_bounds__(256) k_capply_multi(const AT* __restrict__ A, 
   double dot[RMAX];
   capply_multi_body<AT, R_, VJ>(A, cnbr, n, R, x, ypart, nc, dot, reinterpret_cast<typename CV<R_>::T*>(smraw),
                                 shift);
-  if (red.result) grid_reduce<RMAX>(dot, red);
+  if (red.result) grid_reduce<RMAX>(dot, red, R);
 }
 
 template <typename R_>
@@ -1615,7 +1615,7 @@ __global__ void k_ccgm_init(const typename CV<R_>::T* rhs, typename CV<R_>::T* x
       }
     }
   }
-  grid_reduce<RMAX>(v, red);
+  grid_reduce<RMAX>(v, red, R);
 }
 
 __global__ void k_ccgm_start(CCtlM* ctl, int R, double tol, int maxiter) {
@@ -1663,7 +1663,7 @@ __global__ void k_ccgm_update(typename CV<R_>::T* x, typename CV<R_>::T* r, cons
       }
     }
   }
-  grid_reduce<RMAX>(v, red);
+  grid_reduce<RMAX>(v, red, R);
 }
 
 template <typename R_>

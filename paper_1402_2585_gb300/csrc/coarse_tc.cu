@@ -265,12 +265,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
 
   if (w == 0) {
     // ---- producer: bulk copies of A blocks and neighbour B tiles --------------------
-    if (lane == 0) {
-      uint32_t it = 0;
-      bool ok = true;
-      for (int p = blockIdx.x; ok && p < npairs; p += gridDim.x) {
-        const int s0 = p * g.sites;
-        const int site[2] = {s0, min(s0 + 1, g.Vc - 1)};
+    // The whole warp first fetches the pair's 81 (or 162) neighbour indices into
+    // shared memory in one round trip; lane 0 then issues the copies without a
+    // dependent global load in front of every stage.
+    __shared__ int snb[2 * 81];
+    uint32_t it = 0;
+    bool ok = true;
+    for (int p = blockIdx.x; ok && p < npairs; p += gridDim.x) {
+      const int s0 = p * g.sites;
+      const int s1 = min(s0 + 1, g.Vc - 1);
+      for (int q = lane; q < g.sites * 81; q += 32)
+        snb[q] = __ldg(g.cnbr + (size_t)(q < 81 ? s0 : s1) * 81 + q % 81);
+      __syncwarp();
+      if (lane == 0) {
         for (int l = 0; l < 81; ++l, ++it) {
           const int s = (int)(it % (uint32_t)g.stages);
           const uint32_t ph = (it / (uint32_t)g.stages) & 1u;
@@ -282,20 +289,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
           tc::mbar_arrive_expect_tx(TC_FULL(s), stage_bytes);
           const uint32_t dst = ring + (uint32_t)s * stage_bytes;
           // stage: [part 0: site 0, site 1][part 1: site 0, site 1][B site 0][B site 1]
-          for (int p = 0; p < g.parts; ++p)
+          for (int pp = 0; pp < g.parts; ++pp)
             for (int si = 0; si < g.sites; ++si) {
-              const size_t blk = (size_t)site[si] * 81 + l;
-              tc::bulk_g2s(dst + (p * g.sites + si) * g.a_bytes,
-                           reinterpret_cast<const char*>(g.Atc) + (blk * g.parts + p) * g.a_bytes, g.a_bytes,
+              const size_t blk = (size_t)(si ? s1 : s0) * 81 + l;
+              tc::bulk_g2s(dst + (pp * g.sites + si) * g.a_bytes,
+                           reinterpret_cast<const char*>(g.Atc) + (blk * g.parts + pp) * g.a_bytes, g.a_bytes,
                            TC_FULL(s));
             }
           for (int si = 0; si < g.sites; ++si) {
-            const int nb = __ldg(g.cnbr + (size_t)site[si] * 81 + l);
+            const int nb = snb[si * 81 + l];
             tc::bulk_g2s(dst + g.sites * g.parts * g.a_bytes + si * g.b_bytes,
                          reinterpret_cast<const char*>(g.xtc) + (size_t)nb * g.b_bytes, g.b_bytes, TC_FULL(s));
           }
         }
       }
+      ok = __shfl_sync(FULL_MASK, ok ? 1 : 0, 0) != 0;
+      __syncwarp();   // lane 0 is done with snb before the next pair overwrites it
+    }
+    if (lane == 0) {
       // every copy issued has to land before the CTA exits
       const uint32_t first = it > (uint32_t)g.stages ? it - (uint32_t)g.stages : 0u;
       for (uint32_t j = first; j < it; ++j)
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, (uint32_t)g.ncols);
   }
-  if (red.result) grid_reduce<RMAX>(dot, red);
+  if (red.result) grid_reduce<RMAX>(dot, red, g.R);
 }
 
 // ---------------------------------------------------------------------------------
@@ -547,7 +558,7 @@ __global__ void k_cgt_init(const float2* __restrict__ rhs, float2* x, float2* r,
     for (int o = 16; o > 0; o >>= 1) u = fmaxf(u, __shfl_xor_sync(FULL_MASK, u, o));
     if ((threadIdx.x & 31) == 0 && u > 0.f) atomicMax(xmax + q, __float_as_uint(u));
   }
-  grid_reduce<RMAX>(v, red);
+  grid_reduce<RMAX>(v, red, R);
 }
 
 __global__ void k_cgt_start(CCtlT* ctl, int R, double tol, int maxiter) {
@@ -593,7 +604,7 @@ __global__ void k_cgt_update(float2* x, float2* r, const float2* __restrict__ p,
       }
     }
   }
-  grid_reduce<RMAX>(v, red);
+  grid_reduce<RMAX>(v, red, R);
 }
 
 // p = r + beta p for the right-hand sides still running; max|p| of every right-hand side

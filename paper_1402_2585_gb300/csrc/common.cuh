@@ -161,18 +161,33 @@ __device__ __forceinline__ void store_spinor(uint4* __restrict__ f, size_t site5
 // Each block writes NV partial sums to partials[NV * blockIdx.x + i]; the last
 // block to finish (atomic ticket) sums the partials in a fixed order and stores
 // the totals to result[i] (optionally accumulating), then resets the ticket.
+//
+// Multi-right-hand-side kernels reduce NV = k * RED_RHS values laid out as k
+// groups of RED_RHS slots; with `active` right-hand sides, slots whose index
+// modulo RED_RHS is >= active are known to be zero and are skipped (their
+// totals are written as zero).  FP64 adds are slow on GB300, so a reduction
+// of 16 or 32 slots for one right-hand side would otherwise dominate small
+// kernels.
+constexpr int RED_RHS = 16;   // equals RMAX, the right-hand sides per batch
+
 template <int NV>
-__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
+__device__ __forceinline__ bool red_active(int i, int active) {
+  return NV < RED_RHS || (i % RED_RHS) < active;
 }
 
 template <int NV>
-__device__ void block_sum(double (&v)[NV]) {
+__device__ __forceinline__ void warp_sum(double (&v)[NV], int active = RED_RHS) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (red_active<NV>(i, active)) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
+}
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], int active = RED_RHS) {
   __shared__ double sh[32][NV];
-  warp_sum<NV>(v);
+  warp_sum<NV>(v, active);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
   if (lane == 0)
@@ -182,7 +197,7 @@ __device__ void block_sum(double (&v)[NV]) {
   if (w == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = lane < nw ? sh[lane][i] : 0.0;
-    warp_sum<NV>(v);
+    warp_sum<NV>(v, active);
   }
 }
 
@@ -199,8 +214,8 @@ struct Reduction {
 
 // Returns true in every thread of the last block (after the totals are stored).
 template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], const Reduction& red) {
-  block_sum<NV>(v);
+__device__ bool grid_reduce(double (&v)[NV], const Reduction& red, int active = RED_RHS) {
+  block_sum<NV>(v, active);
   __shared__ bool last;
   const unsigned y = blockIdx.y;
   double* partials = red.partials + (size_t)NV * gridDim.x * y;
@@ -221,8 +236,9 @@ __device__ bool grid_reduce(double (&v)[NV], const Reduction& red) {
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[NV * b + i];
-  block_sum<NV>(acc);
+    for (int i = 0; i < NV; ++i)
+      if (red_active<NV>(i, active)) acc[i] += ((volatile double*)partials)[NV * b + i];
+  block_sum<NV>(acc, active);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) result[i] = red.accumulate ? result[i] + acc[i] : acc[i];

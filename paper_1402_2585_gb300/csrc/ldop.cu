@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(YE * YG) k_defl_y(const float2* __restrict__ W
         v[RMAX + qq] += dd;
       }
   }
-  grid_reduce<2 * RMAX>(v, red);
+  grid_reduce<2 * RMAX>(v, red, R);
 }
 
 __global__ void k_ad1_init(const float2* __restrict__ b, float2* x, float2* r, float2* y, size_t ne, int R,
@@ -372,7 +372,7 @@ __global__ void k_ad1_init(const float2* __restrict__ b, float2* x, float2* r, f
         r[t * R + q] = bv;
         v[q] = (double)bv.x * bv.x + (double)bv.y * bv.y;
       }
-  grid_reduce<RMAX>(v, red);
+  grid_reduce<RMAX>(v, red, R);
 }
 
 __global__ void k_ad1_start(CCtlD* ctl, int R, double tol, int maxiter) {
@@ -426,7 +426,7 @@ __global__ void k_ad1_update(float2* x, float2* r, const float2* __restrict__ p,
       }
     }
   // the last block, after every block has updated its part, books the iteration
-  if (grid_reduce<RMAX>(v, red) && threadIdx.x == 0) {
+  if (grid_reduce<RMAX>(v, red, R) && threadIdx.x == 0) {
     const int it = ctl->iter + 1;
     ctl->iter = it;
     int all = 1;

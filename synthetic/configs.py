@@ -29,6 +29,11 @@ class Workload:
     nvec2: int = 0
     seed: int = 0
     antiperiodic_t: bool = False
+    # second-level deflation vectors of the little Dirac operator used by default
+    # (0: plain coarse CG).  At m = 0.002 and below, lam_min / lam_max of the
+    # coarse operator (~1e-6) is at the level of its FP32 rounding, so the
+    # deflation's 1/lam factors are unreliable there; those workloads default to 0.
+    ldop_nvec: int = 0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -56,7 +61,7 @@ WORKLOADS = {
     # FP32 fine operator, two-level HDCG
     "cfg2_16x16x16x16_ls16_shamir": Workload(
         "cfg2_16x16x16x16_ls16_shamir", (16, 16, 16, 16), 16, 1.8, 1.0, 0.0, 0.005, 0.35,
-        (4, 4, 4, 4), 24, 1e-8, "f32", seed=2),
+        (4, 4, 4, 4), 24, 1e-8, "f32", seed=2, ldop_nvec=64),
     # FP16 storage, Moebius
     "cfg3_24x24x24x48_ls16_mobius": Workload(
         "cfg3_24x24x24x48_ls16_mobius", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.002, 0.4,
