@@ -229,6 +229,14 @@ int hdcg_build_coarse_deflation(hdcg_t h, const hdcg_ldop_params* p);
  * deflation and reported as lam = +inf. */
 int hdcg_get_coarse_deflation(hdcg_t h, double* lam_host, void* Z_host);
 
+/* The dense third level's diagonalisation (the "prediagonalised" global level
+ * of Sec. 5.2): eigenvalues w (ascending) and eigenvectors V (columns,
+ * complex double row-major n x n, may be NULL) of the Hermitian part of H
+ * (complex double row-major n x n), by cyclic complex Jacobi rotations on the
+ * host.  No handle and no device work.  HDCG_ERR_ARG for n outside 1..4096
+ * or NULL H / w. */
+int hdcg_dense_heev(int n, const double* H, double* w, double* V);
+
 /* ---------------------------------------------------------------------------
  * Solve H x = b
  * ------------------------------------------------------------------------- */

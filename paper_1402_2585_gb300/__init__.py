@@ -8,4 +8,5 @@ binding fails loudly when the library has not been built; there is no CPU
 fallback.
 """
 from .binding import (F16, F32, F64, BF16, BF16T, DF64, ALG_CG, ALG_ADEF2, HdcgError, Hdcg,  # noqa: F401
-                      SubspaceParams, SolveParams, SolveStats, LdopParams, lib, library_path, PREC_NAMES)
+                      SubspaceParams, SolveParams, SolveStats, LdopParams, dense_heev, lib, library_path,
+                      PREC_NAMES)

@@ -84,6 +84,7 @@ _SIGS = {
     "hdcg_coarse_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I)]),
     "hdcg_build_coarse_deflation": (_I, [_P, ctypes.POINTER(LdopParams)]),
     "hdcg_get_coarse_deflation": (_I, [_P, ctypes.POINTER(_D), _P]),
+    "hdcg_dense_heev": (_I, [_I, _P, _P, _P]),
     "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
     "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
     "hdcg_set_profiling": (_I, [_P, _I]),
@@ -131,6 +132,19 @@ def _ptr(x):
 
 def _on_device(x) -> int:
     return int(bool(getattr(x, "is_cuda", False)))
+
+
+def dense_heev(H, vectors=True):
+    """hdcg_dense_heev: eigenvalues (and eigenvectors) of a Hermitian complex matrix, on the host."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    n = H.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n), dtype=np.complex128) if vectors else None
+    rc = lib().hdcg_dense_heev(n, ctypes.c_void_p(H.ctypes.data), ctypes.c_void_p(w.ctypes.data),
+                               None if V is None else ctypes.c_void_p(V.ctypes.data))
+    if rc != 0:
+        raise HdcgError(rc, "hdcg_dense_heev failed")
+    return (w, V) if vectors else w
 
 
 class Hdcg:

@@ -353,6 +353,16 @@ int hdcg_get_coarse_deflation(hdcg_t h, double* lam_host, void* Z_host) {
   return HDCG_OK;
 }
 
+int hdcg_dense_heev(int n, const double* H, double* w, double* V) {
+  if (n < 1 || n > 4096 || !H || !w) return HDCG_ERR_ARG;
+  try {
+    dense_heev(n, H, w, V);
+  } catch (...) {
+    return HDCG_ERR_OOM;
+  }
+  return HDCG_OK;
+}
+
 int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y) {
   HDCG_ENTRY(h, {
     check_ptr(x, "x");

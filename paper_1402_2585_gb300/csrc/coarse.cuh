@@ -127,6 +127,8 @@ int coarse_apply_partials(Ctx& c, const Coarse& A, int R, const float2* p, float
 // second-level deflation of the little Dirac operator (ldop.cu)
 void ldop_build(Ctx& c, Coarse& A, const hdcg_ldop_params& prm);
 void ldop_export(Ctx& c, const Coarse& A, double* lam_host, void* Z_host);
+// dense Hermitian eigensolver of the third level (host): H, V complex row-major n x n
+void dense_heev(int n, const double* H, double* w, double* V);
 int coarse_adef1(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
 // n complex Gaussians, splitmix64 stream seed, canonical order (same stream as subspace_noise)
 void coarse_noise(Ctx& c, float2* out, size_t n, uint64_t seed);

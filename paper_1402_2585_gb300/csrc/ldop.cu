@@ -601,6 +601,28 @@ void apply_batch(Ctx& c, Coarse& A, int R, const float2* X, float2* Y, DevMem& p
 
 }  // namespace
 
+// host entry to the third level's dense Hermitian eigensolver (no device work)
+void dense_heev(int n, const double* H, double* w, double* V) {
+  std::vector<cplx> a((size_t)n * n);
+  for (size_t i = 0; i < a.size(); ++i) a[i] = cplx(H[2 * i], H[2 * i + 1]);
+  for (int i = 0; i < n; ++i)   // use the Hermitian part
+    for (int j = 0; j < i; ++j) {
+      const cplx h = 0.5 * (a[(size_t)i * n + j] + std::conj(a[(size_t)j * n + i]));
+      a[(size_t)i * n + j] = h;
+      a[(size_t)j * n + i] = std::conj(h);
+    }
+  for (int i = 0; i < n; ++i) a[(size_t)i * n + i] = a[(size_t)i * n + i].real();
+  std::vector<double> ww;
+  std::vector<cplx> vv;
+  herm_eig(n, a, ww, vv);
+  std::copy(ww.begin(), ww.end(), w);
+  if (V)
+    for (size_t i = 0; i < vv.size(); ++i) {
+      V[2 * i] = vv[i].real();
+      V[2 * i + 1] = vv[i].imag();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
