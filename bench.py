@@ -42,6 +42,26 @@ PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 HOP_F32_TRAFFIC = {DEFAULT_WORKLOAD: 126.2e6}
 
 
+def hop_flops_per_site(w) -> int:
+    """Floating-point operations of one H = Mpc^dag Mpc per 5D site (four hop
+    passes), counted from the operator's structure: each pass does 8 hops of
+    (spin projection 12 + two 3x3 complex matrix-vector products 144 +
+    reconstruction 24) = 1440; M_ee^-1 by log2(Ls) shift-and-add steps is
+    48 log2(Ls) + 24; K = b + c P_s is 72 for Moebius and 24 (a scale) for
+    Shamir, and Moebius applies it to each of the 8 neighbours in pass A;
+    the M_oo terms of passes B and D are 72 + 48, with 24 more for the output
+    scale of pass D."""
+    lg = (w.Ls - 1).bit_length()
+    minv = 48 * lg + 24
+    mob = w.c != 0.0
+    k = 72 if mob else 24
+    pass_a = 1440 + (8 * 72 if mob else 0) + minv + k
+    pass_b = 1440 + 72 + 48
+    pass_c = 1440 + k + minv
+    pass_d = 1440 + k + 72 + 48 + 24
+    return pass_a + pass_b + pass_c + pass_d
+
+
 def replica_seeds(w, rank: int) -> dict:
     """Seeds of rank `rank`'s replica: every rank solves its own independent
     problem of the workload (weak scaling, no data-path collective); rank 0
@@ -333,6 +353,10 @@ def run_ours(args, w):
         return
     peak, peak_kind = peaks()
     achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
+    # flop rate of the same launches: a quarter of one H's flops per site per pass
+    n5 = (int(np.prod(w.dims)) // 2) * w.Ls
+    fl_site = hop_flops_per_site(w)
+    hop_tflops = (n_hop * nrhs * n5 * fl_site / 4) / (hop_ms / 1e3) / 1e12 if hop_ms > 0 else 0.0
     s0 = stats[-1]
     n_h = s0["n_mdagm_outer"] + s0["n_mdagm_sloppy"] + s0["n_mdagm_f64"]
     cpu = None
@@ -355,6 +379,8 @@ def run_ours(args, w):
                      "traffic": HOP_F32_TRAFFIC.get(w.name) if outer == 1 else None,
                      "kernel": "hop_kernel (4 passes per H; FP32 storage)", "launches": n_hop,
                      "avg_launch_us": hop_ms * 1e3 / max(1, n_hop), "peak_kind": f"{peak_kind} HBM copy"},
+        "hop_flops": {"flop_per_site_per_H": fl_site, "achieved": hop_tflops, "unit": "TFLOP/s",
+                      "kernel": "hop_kernel (FP32 storage, the roofline kernel's launches)"},
         "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
