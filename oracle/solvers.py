@@ -20,8 +20,8 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
 * ``adef1``    the A-DEF1 method applied to the little Dirac operator with those
                vectors: V_start = 0, M_1 = M P_L + Q, M_2 = M_3 = 1 (Sec. 5.2,
                "Truncated little Dirac operator as preconditioner"), with the
-               high-mode preconditioner M = 1 (the Chebyshev polynomial of
-               Q_trunc is not part of this oracle).  Reading: Table algos prints
+               high-mode preconditioner M = 1 or M = ``qtrunc_chebyshev``.
+               Reading: Table algos prints
                M_2 = P_R in the A-DEF1 row; with V_start = x that keeps every
                search direction out of span(Z), so the iteration cannot reach
                the deflated part of the solution (with a complete basis P_R = 0).
@@ -32,6 +32,11 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                M_2 = M_3 = 1.  ``flexible=True`` uses the Polak-Ribiere
                (flexible CG) beta = (r_{k+1}, y_{k+1} - y_k) / (r_k, y_k); the
                paper cites Notay's flexible CG without printing beta (reading).
+* ``truncate_stencil``, ``chebyshev_inverse``, ``qtrunc_chebyshev``  the
+               high-mode preconditioner of the A-DEF1 coarse solver: the
+               Chebyshev approximation to the inverse of the range-truncated
+               (0- and 1-hop) little Dirac operator Q_trunc (Sec. 5.2, Table
+               frobnorm, Table hierarchy).
 
 Random numbers drawn by the method (the Gaussian start vectors of the
 subspace) are inputs to these functions.
@@ -41,6 +46,11 @@ Parity: ldop_deflation_space and adef1 are pinned by tests/test_oracle_ldop.py
 the dense little Dirac operator, prediagonal third level, A-DEF1 with the
 complete eigenbasis is a direct solve, A-DEF1 reaches the dense solution in
 fewer iterations than CG).
+truncate_stencil, chebyshev_inverse and qtrunc_chebyshev are pinned by
+tests/test_oracle_chebyshev.py (the scalar residual polynomial against
+numpy's Chebyshev T_n, the 1/T_n(sigma) bound on the spectrum of a dense
+Hermitian matrix, positivity on (0, hi], the 9 kept offsets and Hermiticity
+of Q_trunc, A-DEF1 with M reaching the dense solution in fewer iterations).
 cg, mirs, DeflationSpace and adef2 are pinned by
 tests/test_oracle_solvers.py (true residual, free-field exact solution,
 A-DEF2 invariants Q r_k = 0 and P_L r_k = r_k with exact Q, QH = 1 - P_R in
@@ -165,11 +175,80 @@ def ldop_deflation_space(A, blocking: Blocking, noise, steps: int = 3, shift: fl
     return Zs, AZs, lam
 
 
-def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: bool = True,
-          history=None):
-    """A-DEF1 for A x = b with Q = Z diag(lam)^-1 Z^dag, M = 1 (M_2 = 1, see above).
+def truncate_stencil(A, max_hops: int = 1):
+    """Q_trunc of Sec. 5.2: the stencil restricted to the blocks at most
+    ``max_hops`` block hops (taxicab) away; the 0- and 1-hop terms (9 of the
+    81) for the paper's choice.  Dropping whole (l, -l) pairs keeps it
+    Hermitian."""
+    from .coarse import stencil_offsets
+    hops = np.abs(stencil_offsets()).sum(axis=1)
+    T = np.array(A, copy=True)
+    T[:, hops > max_hops] = 0
+    return T
 
-    x_0 = 0, r_0 = b; y = M_1 r = P_L r + Q r = r - A Q r + Q r; p_0 = y_0; then
+
+def chebyshev_inverse(apply_M, r, order: int, lo: float, hi: float):
+    """p(M) r, the Chebyshev approximation to M^-1 of order ``order`` on the
+    interval [lo, hi] (Sec. 5.2 and Table hierarchy: order 16 on [0.5, 45],
+    applied to Q_trunc).
+
+    Reading: p is the degree order-1 polynomial of Chebyshev acceleration
+    (the minimax polynomials the paper cites from Saad in Sec. 1), defined by
+    1 - x p(x) = T_order((theta - x)/delta) / T_order(theta/delta) with
+    theta = (hi + lo)/2 and delta = (hi - lo)/2.  So |1 - x p(x)| <=
+    1/T_order(theta/delta) on [lo, hi], p > 0 on (0, hi] (a positive
+    definite preconditioner for any M with spectrum there), and lo acts as
+    the infra-red regulator: modes below lo are left partly uncorrected.
+
+    Steps (the three-term recurrence of Chebyshev acceleration from y_0 = 0,
+    s_0 = r): sigma = theta/delta, rho_0 = 1/sigma, d_0 = r/theta; then
+    y_{k+1} = y_k + d_k, s_{k+1} = s_k - M d_k,
+    rho_{k+1} = 1/(2 sigma - rho_k),
+    d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1}/delta) s_{k+1};
+    y_order is returned after order-1 products with M.
+    """
+    if order < 1 or not 0 < lo < hi:
+        raise ValueError("need order >= 1 and 0 < lo < hi")
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    y = np.zeros_like(r)
+    s = np.array(r, copy=True)
+    d = r / theta
+    for k in range(order):
+        y = y + d
+        if k == order - 1:
+            break
+        s = s - apply_M(d)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * s
+        rho = rho_new
+    return y
+
+
+def qtrunc_chebyshev(A, blocking: Blocking, order: int = 16, lo: float = 0.5, hi: float = 45.0,
+                     shift: float = 0.0):
+    """The A-DEF1 high-mode preconditioner of Sec. 5.2 (Table hierarchy):
+    M = p(Q_trunc + shift) with Q_trunc the 0- and 1-hop part of the stencil
+    A and p the order-``order`` Chebyshev approximation to 1/x on [lo, hi].
+    ``shift`` is an explicit infra-red shift of Q_trunc (reading: the paper
+    names one without a value; its tuned parameters give only [lo, hi], so 0
+    by default).  Returns the map r -> M r."""
+    T = truncate_stencil(A, 1)
+
+    def apply_T(v):
+        return coarse_apply(T, v, blocking) + shift * v
+
+    return lambda r: chebyshev_inverse(apply_T, r, order, lo, hi)
+
+
+def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: bool = True,
+          history=None, M=None):
+    """A-DEF1 for A x = b with Q = Z diag(lam)^-1 Z^dag (M_2 = 1, see above) and
+    the high-mode preconditioner M (default 1; the paper's choice is a
+    Chebyshev polynomial of the shifted Q_trunc, ``chebyshev_inverse``).
+
+    x_0 = 0, r_0 = b; y = M_1 r = M P_L r + Q r = M (r - A Q r) + Q r; p_0 = y_0; then
     w = A p, alpha = (r, y)/(p, w), x += alpha p, r -= alpha w, y' = M_1 r,
     beta = (r, y' - y)/(r_old, y_old) (flexible) or (r, y')/(r_old, y_old),
     p = y' + beta p.  A Q v = (A Z) diag(lam)^-1 Z^dag v uses the stored A Z, so
@@ -182,7 +261,9 @@ def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: b
 
     def M1(r):
         d = (Zf.conj() @ r.ravel()) / lam
-        return r + ((Zf - AZf).T @ d).reshape(shape)
+        if M is None:
+            return r + ((Zf - AZf).T @ d).reshape(shape)
+        return M(r - (AZf.T @ d).reshape(shape)) + (Zf.T @ d).reshape(shape)
 
     x = np.zeros_like(b)
     r = np.array(b, copy=True)

@@ -17,3 +17,26 @@ def golden():
     import json
     with open(os.path.join(ROOT, "tests", "golden", "paper_facts.json")) as f:
         return json.load(f)
+
+
+@pytest.fixture(scope="session")
+def little_dirac_12x12x4x4():
+    """Little Dirac operator of a 12x12x4x4, Ls 4 Mobius lattice: coarse grid
+    3x3x1x1, Nvec 4 from inverse iteration (dimension 36, spectrum 0.18 .. 6.5
+    with four isolated low modes).  Built once: the brute-force assembly takes
+    about 40 s.  Returns (dwf, blocking, phi, stencil, dense, eigenvalues)."""
+    import numpy as np
+
+    import synthetic as sy
+    from oracle.coarse import Blocking, coarse_dense_bruteforce, dense_to_stencil, stencil_to_dense
+    from oracle.dwf import DWF
+    from oracle.solvers import inverse_iteration_subspace
+
+    dims, Ls = (12, 12, 4, 4), 4
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.01, sy.gauge_field(dims, 0.4, 1200))
+    bl = Blocking(d, (4, 4, 4, 4))
+    phi = inverse_iteration_subspace(d.mdagm, sy.gaussian_fermions(dims, Ls, 1201, 4), bl, steps=2, tol=1e-4)
+    A = dense_to_stencil(coarse_dense_bruteforce(d.mdagm, phi, bl), bl)
+    n = bl.Vc * 4
+    Dn = stencil_to_dense(A, bl).reshape(n, n)
+    return d, bl, phi, A, Dn, np.linalg.eigvalsh(Dn)

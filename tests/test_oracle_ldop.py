@@ -15,23 +15,14 @@ import numpy as np
 import pytest
 
 import synthetic as sy
-from oracle.coarse import Blocking, coarse_apply, coarse_dense_bruteforce, dense_to_stencil, stencil_to_dense
-from oracle.dwf import DWF, norm2
-from oracle.solvers import DeflationSpace, adef1, adef2, cg, inverse_iteration_subspace, ldop_deflation_space
+from oracle.coarse import coarse_apply
+from oracle.dwf import norm2
+from oracle.solvers import DeflationSpace, adef1, adef2, cg, ldop_deflation_space
 
 
 @pytest.fixture(scope="module")
-def ldop():
-    """Little Dirac operator of a 12x12x4x4, Ls 4 Mobius lattice: coarse grid
-    3x3x1x1, Nvec 4 from inverse iteration (dimension 36, ill-conditioned)."""
-    dims, Ls = (12, 12, 4, 4), 4
-    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.01, sy.gauge_field(dims, 0.4, 1200))
-    bl = Blocking(d, (4, 4, 4, 4))
-    phi = inverse_iteration_subspace(d.mdagm, sy.gaussian_fermions(dims, Ls, 1201, 4), bl, steps=2, tol=1e-4)
-    A = dense_to_stencil(coarse_dense_bruteforce(d.mdagm, phi, bl), bl)
-    n = bl.Vc * 4
-    Dn = stencil_to_dense(A, bl).reshape(n, n)
-    return d, bl, phi, A, Dn, np.linalg.eigvalsh(Dn)
+def ldop(little_dirac_12x12x4x4):
+    return little_dirac_12x12x4x4
 
 
 def _apply(A, bl):
