@@ -427,7 +427,7 @@ int hdcg_set_profiling(hdcg_t h, int on) {
       for (int i = 0; i < PH_N; ++i) c.phases.ms[i] = 0;
     c.prof.on = on != 0;
     if (on) {
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < NPREC; ++i) {
         c.prof.launches[i] = 0;
         c.prof.ms[i] = 0;
         c.prof.bytes[i] = 0;
