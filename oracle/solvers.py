@@ -246,7 +246,8 @@ def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: b
           history=None, M=None):
     """A-DEF1 for A x = b with Q = Z diag(lam)^-1 Z^dag (M_2 = 1, see above) and
     the high-mode preconditioner M (default 1; the paper's choice is a
-    Chebyshev polynomial of the shifted Q_trunc, ``chebyshev_inverse``).
+    Chebyshev polynomial of the shifted Q_trunc, ``qtrunc_chebyshev``).
+    With no vectors (nd = 0) this is CG preconditioned by M.
 
     x_0 = 0, r_0 = b; y = M_1 r = M P_L r + Q r = M (r - A Q r) + Q r; p_0 = y_0; then
     w = A p, alpha = (r, y)/(p, w), x += alpha p, r -= alpha w, y' = M_1 r,
@@ -255,8 +256,8 @@ def adef1(apply_A, b, Z, AZ, lam, tol: float, maxiter: int = 100000, flexible: b
     every iteration applies A once.  Returns (x, iterations).
     """
     nd = Z.shape[0]
-    Zf = Z.reshape(nd, -1)
-    AZf = AZ.reshape(nd, -1)
+    Zf = Z.reshape(nd, b.size)
+    AZf = AZ.reshape(nd, b.size)
     shape = b.shape
 
     def M1(r):
