@@ -50,7 +50,8 @@ truncate_stencil, chebyshev_inverse and qtrunc_chebyshev are pinned by
 tests/test_oracle_chebyshev.py (the scalar residual polynomial against
 numpy's Chebyshev T_n, the 1/T_n(sigma) bound on the spectrum of a dense
 Hermitian matrix, positivity on (0, hi], the 9 kept offsets and Hermiticity
-of Q_trunc, A-DEF1 with M reaching the dense solution in fewer iterations).
+of Q_trunc, A-DEF1 with M reaching the dense solution in fewer iterations,
+and with no vectors reducing to CG, preconditioned or not).
 cg, mirs, DeflationSpace and adef2 are pinned by
 tests/test_oracle_solvers.py (true residual, free-field exact solution,
 A-DEF2 invariants Q r_k = 0 and P_L r_k = r_k with exact Q, QH = 1 - P_R in

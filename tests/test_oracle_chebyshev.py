@@ -21,7 +21,7 @@ from numpy.polynomial import chebyshev as C
 import synthetic as sy
 from oracle.coarse import Blocking, coarse_apply, dense_to_stencil, stencil_to_dense
 from oracle.dwf import DWF, norm2
-from oracle.solvers import adef1, chebyshev_inverse, ldop_deflation_space, qtrunc_chebyshev, truncate_stencil
+from oracle.solvers import adef1, cg, chebyshev_inverse, ldop_deflation_space, qtrunc_chebyshev, truncate_stencil
 
 
 def _scalar_p(x, order, lo, hi):
@@ -167,3 +167,26 @@ def test_adef1_with_chebyshev_qtrunc_converges_faster(ldop, flexible):
     x, it = adef1(apply_A, b, Z, AZ, lam, 1e-10, flexible=flexible, M=M)
     assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-8
     assert it < it1 / 2
+
+
+def test_empty_deflation_space_is_preconditioned_cg(ldop):
+    """With no deflation vectors A-DEF1 is CG preconditioned by M: the dense
+    solution in fewer iterations than plain CG, and with M = 1 exactly CG's
+    iterates."""
+    bl, A, Dn = ldop
+    n = Dn.shape[0]
+    b = sy.coarse_gaussian(bl.Vc, 4, 1330)
+    xs = np.linalg.solve(Dn, b.ravel()).reshape(b.shape)
+
+    def apply_A(v):
+        return coarse_apply(A, v, bl)
+
+    Z0 = np.zeros((0, bl.Vc, 4), dtype=np.complex128)
+    Tn = stencil_to_dense(truncate_stencil(A), bl).reshape(n, n)
+    M = qtrunc_chebyshev(A, bl, 16, 0.05, 1.1 * np.linalg.eigvalsh(Tn)[-1])
+    x, it = adef1(apply_A, b, Z0, Z0, np.zeros(0), 1e-10, M=M)
+    assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-8
+    x1, it1 = adef1(apply_A, b, Z0, Z0, np.zeros(0), 1e-10, flexible=False)
+    xc, itc = cg(apply_A, b, 1e-10)
+    assert it1 == itc and np.abs(x1 - xc).max() < 1e-10 * np.abs(xc).max()
+    assert it < itc
