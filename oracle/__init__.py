@@ -18,7 +18,11 @@ Modules
              the coarse stencil apply (Sec. 2, Sec. 5.1, Sec. 5.1.1).
 ``solvers``  CG, the infra-red shifted smoother M_IRS, inverse-iteration
              subspace, A-DEF2 with flexible beta (Figs. pcg / pcg_general,
-             Table algos, Sec. 4.3).
+             Table algos, Sec. 4.3); second-level global deflation and A-DEF1
+             with the Chebyshev preconditioner on Q_trunc (Sec. 5.2).
+``level2``   blocks of the coarse lattice: the blocked second coarsening of
+             a three-level hierarchy (Sec. 2 applied to the little Dirac
+             operator).
 
 Parity status of each function is stated in its docstring; every function
 here is pinned by a ``-m "not gpu"`` test except where marked

@@ -307,6 +307,10 @@ class DeflationSpace:
     coarse_maxiter: int = 100000
     coarse_iters: list = field(default_factory=list)
     ldop: tuple = None             # (Z, AZ, lam): coarse solve by A-DEF1 with these vectors
+    # blocked second level (oracle.level2): the coarse solve is A-DEF2 on A with
+    # this DeflationSpace of coarse vectors and the smoother level2_M (None: M = 1)
+    level2: object = None
+    level2_M: object = None
 
     def __post_init__(self):
         self._dense = None
@@ -322,7 +326,11 @@ class DeflationSpace:
         if self.coarse_tol == 0.0:
             return np.linalg.solve(self.dense(), c.ravel()).reshape(c.shape)
         Aop = lambda v: coarse_apply(self.A, v, self.blocking)
-        if self.ldop is not None:
+        if self.level2 is not None:
+            M = self.level2_M if self.level2_M is not None else (lambda v: v)
+            res = adef2(Aop, c, self.level2, self.coarse_tol, self.coarse_maxiter, M=M)
+            y, it = res.x, res.iterations
+        elif self.ldop is not None:
             y, it = adef1(Aop, c, *self.ldop, self.coarse_tol, self.coarse_maxiter)
         else:
             y, it = cg(Aop, c, self.coarse_tol, self.coarse_maxiter)
@@ -350,7 +358,7 @@ class SolveResult:
 
 def adef2(apply_H, b, defl: DeflationSpace, tol: float, maxiter: int = 10000,
           mirs_iter: int = 7, mirs_shift: float = 1.0, flexible: bool = True,
-          x_guess=None, track_invariants: bool = False, apply_H_sloppy=None):
+          x_guess=None, track_invariants: bool = False, apply_H_sloppy=None, M=None):
     """A-DEF2 preconditioned CG (Fig. pcg_general, Table algos row A-DEF2).
 
     x_0 = Q b + P_R x (x = x_guess or 0), r_0 = b - H x_0,
@@ -359,6 +367,8 @@ def adef2(apply_H, b, defl: DeflationSpace, tol: float, maxiter: int = 10000,
     r -= alpha w, y' = M_1 r, beta (flexible or standard), p = y' + beta p.
     Stops when the recursive residual reaches ``tol``; returns the true residual.
     ``apply_H_sloppy`` (default: ``apply_H``) is the operator inside M_1.
+    ``M`` replaces M_IRS by another smoother z = M r (the level-1 solve of the
+    three-level method uses M = 1 or the Chebyshev of Q_trunc).
     """
     Hs = apply_H if apply_H_sloppy is None else apply_H_sloppy
     Q = defl.Q
@@ -370,7 +380,7 @@ def adef2(apply_H, b, defl: DeflationSpace, tol: float, maxiter: int = 10000,
     bb = _n2(b)
 
     def M1(res):
-        z = mirs(Hs, res, mirs_iter, mirs_shift)
+        z = mirs(Hs, res, mirs_iter, mirs_shift) if M is None else M(res)
         return z + Q(res - Hs(z))
 
     y = M1(r)
