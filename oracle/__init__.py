@@ -20,6 +20,8 @@ Modules
              subspace, A-DEF2 with flexible beta (Figs. pcg / pcg_general,
              Table algos, Sec. 4.3); second-level global deflation and A-DEF1
              with the Chebyshev preconditioner on Q_trunc (Sec. 5.2).
+``subspace`` subspace generation by the rational low-pass filter: multi-shift
+             CG, wall-placed noise, surface truncation (Sec. 4.2).
 ``level2``   blocks of the coarse lattice: the blocked second coarsening of
              a three-level hierarchy (Sec. 2 applied to the little Dirac
              operator).

@@ -1,0 +1,114 @@
+"""Pins of the oracle's rational-filter subspace generation (Sec. 4.2, Eq.
+ratfilt, Table FineSubspaceParams).  No GPU.
+
+What fixes them, independently of the oracle's own code:
+* the partial fractions against the product prod_i 1/(x + sigma_i) at
+  sample points (closed form);
+* multi-shift solutions against numpy's dense solves of every shifted
+  system, and with a single shift the textbook CG, iterate by iterate;
+* the filter against the eigendecomposition of a dense Hermitian matrix
+  (numpy's eigh);
+* the support and chirality of the wall noise (gamma_5 eigenvalues);
+* the filtered subspace of a domain wall operator concentrating on its low
+  end of the spectrum (Rayleigh quotients far below those of the noise).
+"""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle.coarse import Blocking
+from oracle.dwf import DWF, gamma_matrices
+from oracle.solvers import cg
+from oracle.subspace import (multishift_cg, rational_filter, rational_filter_shifts, rational_subspace,
+                             surface_truncate, wall_noise)
+
+
+def _hpd(n, seed, lo=1e-3, hi=10.0):
+    U, _ = np.linalg.qr(sy.complex_normal(seed, (n, n)))
+    ev = np.geomspace(lo, hi, n)
+    return (U * ev) @ U.conj().T, ev, U
+
+
+@pytest.mark.parametrize("lam,eps", [(0.0003, 0.0001), (0.5, 0.25), (1e-2, 1e-2)])
+def test_partial_fractions(lam, eps):
+    sig, c = rational_filter_shifts(lam, eps)
+    assert sig == pytest.approx([lam, lam + eps, lam + 2 * eps, lam + 3 * eps])
+    for x in [0.0, 1e-4, 0.01, 1.0, 37.0]:
+        prod = 1.0 / np.prod([x + s for s in sig])
+        terms = [ci / (x + si) for ci, si in zip(c, sig)]
+        # the weights grow like eps^-3, so the sum cancels: its rounding error is
+        # bounded by a few ulps of the largest term (the filter's high-mode
+        # response is then tiny in absolute terms, far below its low-mode one)
+        assert abs(sum(terms) - prod) <= 1e-15 * max(abs(t) for t in terms) * 8
+
+
+def test_multishift_solves_every_shifted_system():
+    H, ev, U = _hpd(60, 1700)
+    b = sy.complex_normal(1701, (60,))
+    shifts = [0.3, 0.0, 1e-2, 2.0]
+    xs, it = multishift_cg(lambda v: H @ v, b, shifts, 1e-12)
+    for s, x in zip(shifts, xs):
+        want = np.linalg.solve(H + s * np.eye(60), b)
+        assert np.linalg.norm(x - want) <= 1e-8 * np.linalg.norm(want)
+        assert np.linalg.norm(b - (H @ x + s * x)) <= 1e-10 * np.linalg.norm(b)
+    # the base system (the smallest shift) runs exactly the textbook CG
+    _, itc = cg(lambda v: H @ v, b, 1e-12)
+    assert it == itc
+
+
+def test_single_shift_is_textbook_cg():
+    H, ev, U = _hpd(40, 1702, lo=0.05)
+    b = sy.complex_normal(1703, (40,))
+    for n in [1, 3, 10]:
+        xs, it = multishift_cg(lambda v: H @ v, b, [0.0], 0.0, maxiter=n)
+        xc, itc = cg(lambda v: H @ v, b, 0.0, maxiter=n)
+        assert it == itc == n
+        assert np.abs(xs[0] - xc).max() < 1e-12 * np.abs(xc).max()
+
+
+def test_filter_against_eigendecomposition():
+    H, ev, U = _hpd(50, 1704, lo=1e-4, hi=5.0)
+    eta = sy.complex_normal(1705, (50,))
+    lam, eps = 3e-4, 1e-4
+    phi = rational_filter(lambda v: H @ v, eta, lam, eps, 1e-13)
+    resp = 1.0 / np.prod([ev + lam + i * eps for i in range(4)], axis=0)
+    want = U @ (resp * (U.conj().T @ eta))
+    assert np.linalg.norm(phi - want) <= 1e-7 * np.linalg.norm(want)
+    # a fourth-order low-pass filter: x^4 times the response tends to 1
+    assert abs(resp[-1] * ev[-1] ** 4 - 1) < 6 * (lam + 3 * eps) / ev[-1]
+
+
+def test_wall_noise_support_and_chirality():
+    n4, Ls = 10, 6
+    eta = wall_noise(n4, Ls, 3, 1706)
+    assert eta.shape == (3, n4, Ls, 4, 3)
+    assert np.all(eta[:, :, 1:Ls - 1] == 0)
+    _, g5 = gamma_matrices()
+    # s = 0 holds gamma_5 = -1 components only, s = Ls - 1 gamma_5 = +1 only
+    assert np.allclose(np.einsum("ab,kxbc->kxac", g5, eta[:, :, 0]), -eta[:, :, 0])
+    assert np.allclose(np.einsum("ab,kxbc->kxac", g5, eta[:, :, Ls - 1]), eta[:, :, Ls - 1])
+    xi = sy.complex_normal(1706, (3, n4, 4, 3))
+    assert np.allclose(eta[:, :, 0] + eta[:, :, Ls - 1], xi)
+
+
+def test_surface_truncation():
+    phi = sy.complex_normal(1707, (2, 5, 8, 4, 3))
+    t = surface_truncate(phi, 2)
+    assert np.array_equal(t[:, :, :2], phi[:, :, :2]) and np.array_equal(t[:, :, 6:], phi[:, :, 6:])
+    assert np.all(t[:, :, 2:6] == 0)
+    assert np.array_equal(surface_truncate(phi, 4), phi)
+
+
+def test_rational_subspace_concentrates_on_low_modes():
+    """Domain wall operator 8x4x4x4, Ls 4: the filtered vectors' Rayleigh
+    quotients lie far below those of the wall noise and of Gaussian vectors."""
+    dims, Ls = (8, 4, 4, 4), 4
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.02, sy.gauge_field(dims, 0.4, 1708))
+    bl = Blocking(d, (4, 4, 4, 4))
+    phi = rational_subspace(d.mdagm, bl, 4, 1709, lam=0.05, eps=0.02, tol=1e-6)
+    def rq(v):
+        return np.vdot(v, d.mdagm(v)).real / np.vdot(v, v).real
+    q_phi = max(rq(v) for v in phi)
+    q_noise = min(rq(v) for v in wall_noise(d.lat.V // 2, Ls, 4, 1709))
+    q_gauss = min(rq(v) for v in sy.gaussian_fermions(dims, Ls, 1710, 4))
+    assert q_phi < 0.1 * q_noise and q_phi < 0.1 * q_gauss
