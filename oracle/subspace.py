@@ -24,20 +24,37 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
 * ``surface_truncate``  SubspaceSurfaceDepth: the s-slices farther than
                ``depth`` from both walls set to zero.
 * ``rational_subspace``  wall noise, the filter, block Gram-Schmidt.
+* ``promote``  a field of a reduced fifth dimension Ls1 placed into Ls: the
+               half of the s-slices nearer each wall keeps its distance to that
+               wall, the bulk between is zero ("promoted to the surface regions
+               of the full system").
+* ``two_pass_subspace``  the two-stage generation (Sec. 4.2, Table optimised,
+               first and second pass controls): the filter on a reduced-Ls
+               operator with its own mass, promotion, then one shifted inversion
+               (H + lam2)^-1 of every promoted vector on the full system by
+               A-DEF2 deflated with the promoted vectors (the "first pass
+               deflated solver"), to a loose residual, and block Gram-Schmidt.
+               Reading: the deflation space of the second pass is the block
+               Gram-Schmidt of the promoted vectors, its coarse operator that of
+               H + lam2 (A + lam2 on the diagonal blocks, exact for orthonormal
+               blocks), the smoother M_IRS as in the solver.
 
 Parity: pinned by tests/test_oracle_subspace.py (the partial fractions
 against the product at sample points; multi-shift solutions against numpy's
 dense solves and, for one shift, against the textbook CG iterate by iterate;
 the filter against the eigendecomposition of a dense Hermitian matrix; the
 support and chirality of the wall noise; the truncation; the filtered
-subspace of a domain wall operator concentrating on its low modes).
+subspace of a domain wall operator concentrating on its low modes; the
+promotion's placement; the two-pass result solving its shifted systems, equal
+to the single pass when Ls1 = Ls without refinement, and concentrating on the
+low modes).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .coarse import Blocking, block_gram_schmidt
-from .dwf import gamma_matrices
+from .coarse import Blocking, block_gram_schmidt, coarse_dense_bruteforce, dense_to_stencil
+from .dwf import DWF, gamma_matrices
 
 
 def _dot(a, b):
@@ -166,3 +183,43 @@ def rational_subspace(apply_H, blocking: Blocking, nvec: int, seed: int, lam: fl
     if depth:
         phi = surface_truncate(phi, depth)
     return block_gram_schmidt(phi, blocking)
+
+
+def promote(phi, Ls: int):
+    """(..., n4, Ls1, 4, 3) -> (..., n4, Ls, 4, 3): slices s < ceil(Ls1/2) stay
+    at s, slices s >= ceil(Ls1/2) move to s + Ls - Ls1, the bulk is zero."""
+    Ls1 = phi.shape[-3]
+    if Ls1 > Ls:
+        raise ValueError("the first-pass fifth dimension must not exceed Ls")
+    h = (Ls1 + 1) // 2
+    shape = phi.shape[:-3] + (Ls,) + phi.shape[-2:]
+    out = np.zeros(shape, dtype=np.complex128)
+    out[..., :h, :, :] = phi[..., :h, :, :]
+    out[..., Ls - (Ls1 - h):, :, :] = phi[..., h:, :, :]
+    return out
+
+
+def two_pass_subspace(d: DWF, blocking: Blocking, nvec: int, seed: int, Ls1: int, mass1: float, lam: float,
+                      eps: float, tol1: float, lam2: float = 0.0, tol2: float = 1e-3, depth: int = 0,
+                      mirs_iter: int = 7, mirs_shift: float = 1.0):
+    """The two-stage subspace: the rational filter on the Ls1, mass1 operator
+    (same gauge field and 4D lattice), promotion to Ls, and with lam2 > 0 one
+    solve of (H + lam2) x = v per promoted vector v by A-DEF2 deflated with
+    the promoted vectors (relative residual tol2), then the surface truncation
+    (depth > 0) and block Gram-Schmidt."""
+    from .solvers import DeflationSpace, adef2
+    d1 = DWF(d.lat.dims, Ls1, d.M5, d.b, d.c, mass1, d.U, antiperiodic_t=d.apbc)
+    eta = wall_noise(d.lat.V // 2, Ls1, nvec, seed)
+    phi1 = np.stack([rational_filter(d1.mdagm, e, lam, eps, tol1) for e in eta])
+    v = promote(phi1, d.Ls)
+    if lam2 > 0:
+        def Hs(x):
+            return d.mdagm(x) + lam2 * x
+        basis = block_gram_schmidt(v, blocking)
+        A = dense_to_stencil(coarse_dense_bruteforce(d.mdagm, basis, blocking), blocking)
+        A[:, 40] += lam2 * np.eye(nvec)
+        defl = DeflationSpace(basis, blocking, A, coarse_tol=0.0)
+        v = np.stack([adef2(Hs, vk, defl, tol2, mirs_iter=mirs_iter, mirs_shift=mirs_shift).x for vk in v])
+    if depth:
+        v = surface_truncate(v, depth)
+    return block_gram_schmidt(v, blocking)

@@ -19,8 +19,8 @@ import synthetic as sy
 from oracle.coarse import Blocking
 from oracle.dwf import DWF, gamma_matrices
 from oracle.solvers import cg
-from oracle.subspace import (multishift_cg, rational_filter, rational_filter_shifts, rational_subspace,
-                             surface_truncate, wall_noise)
+from oracle.subspace import (multishift_cg, promote, rational_filter, rational_filter_shifts, rational_subspace,
+                             surface_truncate, two_pass_subspace, wall_noise)
 
 
 def _hpd(n, seed, lo=1e-3, hi=10.0):
@@ -112,3 +112,50 @@ def test_rational_subspace_concentrates_on_low_modes():
     q_noise = min(rq(v) for v in wall_noise(d.lat.V // 2, Ls, 4, 1709))
     q_gauss = min(rq(v) for v in sy.gaussian_fermions(dims, Ls, 1710, 4))
     assert q_phi < 0.1 * q_noise and q_phi < 0.1 * q_gauss
+
+
+def test_promote_places_the_surfaces():
+    phi = sy.complex_normal(1711, (2, 5, 4, 4, 3))
+    out = promote(phi, 10)
+    assert out.shape == (2, 5, 10, 4, 3)
+    assert np.array_equal(out[:, :, :2], phi[:, :, :2])
+    assert np.array_equal(out[:, :, 8:], phi[:, :, 2:])
+    assert np.all(out[:, :, 2:8] == 0)
+    odd = sy.complex_normal(1712, (5, 3, 4, 3))
+    o2 = promote(odd, 7)          # Ls1 = 3: slices 0, 1 near the first wall, 2 at the last
+    assert np.array_equal(o2[:, :2], odd[:, :2]) and np.array_equal(o2[:, 6], odd[:, 2])
+    assert np.all(o2[:, 2:6] == 0)
+    assert np.array_equal(promote(phi, 4), phi)
+    with pytest.raises(ValueError):
+        promote(phi, 3)
+
+
+@pytest.fixture(scope="module")
+def dwf8():
+    dims, Ls = (8, 4, 4, 4), 8
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.02, sy.gauge_field(dims, 0.4, 1713))
+    return d, Blocking(d, (4, 4, 4, 4))
+
+
+def test_two_pass_without_refinement_at_full_ls_is_the_single_pass():
+    dims = (8, 4, 4, 4)
+    d = DWF(dims, 4, 1.8, 1.5, 0.5, 0.02, sy.gauge_field(dims, 0.4, 1713))
+    bl = Blocking(d, (4, 4, 4, 4))
+    a = two_pass_subspace(d, bl, 2, 1714, d.Ls, d.mass, 0.05, 0.02, 1e-8)
+    b = rational_subspace(d.mdagm, bl, 2, 1714, 0.05, 0.02, tol=1e-8)
+    assert np.abs(a - b).max() < 1e-12
+
+
+def test_two_pass_refined_subspace(dwf8):
+    """First pass at Ls 4 with a heavier mass, promotion to Ls 8, one deflated
+    shifted inversion per vector: the vectors concentrate on the low end
+    (Rayleigh quotients well below those of Gaussian vectors) and on the walls."""
+    d, bl = dwf8
+    phi = two_pass_subspace(d, bl, 3, 1715, 4, 0.05, 0.05, 0.02, 1e-6, lam2=1e-3, tol2=1e-3)
+    def rq(v):
+        return np.vdot(v, d.mdagm(v)).real / np.vdot(v, v).real
+    q_phi = max(rq(v) for v in phi)
+    q_gauss = min(rq(v) for v in sy.gaussian_fermions(d.lat.dims, d.Ls, 1716, 3))
+    assert q_phi < 0.1 * q_gauss
+    w = np.sqrt((np.abs(phi) ** 2).sum(axis=(1, 3, 4)))   # (nvec, Ls) weight per s-slice
+    assert np.all(w[:, [0, -1]].sum(axis=1) > w[:, 3:5].sum(axis=1))
