@@ -20,6 +20,9 @@ Modules
              subspace, A-DEF2 with flexible beta (Figs. pcg / pcg_general,
              Table algos, Sec. 4.3); second-level global deflation and A-DEF1
              with the Chebyshev preconditioner on Q_trunc (Sec. 5.2).
+``pcg_family`` the generalised preconditioned CG of Fig. pcg_general with the
+             rows of Table algos (PREC, AD, DEF1, DEF2, A-DEF1, A-DEF2, BNN,
+             V(1,1)) and the frozen CG polynomial M_IRSpoly (Sec. 4.5).
 ``subspace`` subspace generation by the rational low-pass filter: multi-shift
              CG, wall-placed noise, surface truncation (Sec. 4.2).
 ``level2``   blocks of the coarse lattice: the blocked second coarsening of
