@@ -137,6 +137,15 @@ def spin_mul(G, psi):
     return np.matmul(G, psi)
 
 
+def twisted_gauge(U, theta):
+    """Links for twisted boundary conditions (Sec. 6.4, "Subspace reuse", Table
+    twist): psi(x + L_mu) = e^{i L_mu theta_mu} psi(x) is, after the U(1) gauge
+    transformation psi -> e^{-i theta.x} psi, the same operator as uniform link
+    phases U_mu(x) -> e^{i theta_mu} U_mu(x); the paper's twist (pi/L)(a, b, c)
+    is theta_mu = pi a_mu / L_mu."""
+    return np.asarray(U, dtype=np.complex128) * np.exp(1j * np.asarray(theta, dtype=float))[None, :, None, None]
+
+
 # ----------------------------------------------------------------------------
 # fifth-dimension operators (site independent, real, 4Ls x 4Ls over (s, spin))
 # ----------------------------------------------------------------------------
