@@ -23,6 +23,8 @@ Modules
 ``pcg_family`` the generalised preconditioned CG of Fig. pcg_general with the
              rows of Table algos (PREC, AD, DEF1, DEF2, A-DEF1, A-DEF2, BNN,
              V(1,1)) and the frozen CG polynomial M_IRSpoly (Sec. 4.5).
+``codec``    reduced-precision spinor codecs: 16-bit truncation and the 8-bit
+             format with a half-precision prefactor (Sec. 6.5).
 ``subspace`` subspace generation by the rational low-pass filter: multi-shift
              CG, wall-placed noise, surface truncation (Sec. 4.2).
 ``level2``   blocks of the coarse lattice: the blocked second coarsening of

@@ -1,0 +1,85 @@
+"""Pins of the reduced-precision spinor codecs (Sec. 6.5, Table sloppy).  No
+GPU.  What fixes them: the IEEE bit patterns of the truncation; the 8-bit
+round-trip bound; exact zeros; and an HDCG solve with the codec applied to
+the M_IRS input converging in about as many outer iterations as without
+(Table sloppy: no change for 16 bits)."""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle.codec import bytes_i8_per_site, decode_i8, encode_i8, truncate16
+from oracle.coarse import Blocking, coarse_dense_bruteforce, dense_to_stencil
+from oracle.dwf import DWF, norm2
+from oracle.solvers import DeflationSpace, adef2, inverse_iteration_subspace, mirs
+
+
+def test_truncate16_bit_pattern():
+    x = np.array([1.0, -1.0, 3.14159265, 1e-3, 65504.0, 0.0, 1.0 + 2 ** -8])
+    t = truncate16(x)
+    for a, b in zip(x, t):
+        fa = np.float32(a).view(np.uint32)
+        assert np.float32(b).view(np.uint32) == (fa & 0xFFFF0000)
+    # 7 mantissa bits: relative error below 2^-7, never rounded up in magnitude
+    y = sy.complex_normal(1960, (100,))
+    ty = truncate16(y)
+    for a, b in [(y.real, ty.real), (y.imag, ty.imag)]:
+        assert np.all(np.abs(a - b) <= 2.0 ** -7 * np.abs(a) * 1.0000001)
+        assert np.all(np.abs(b) <= np.abs(a) * (1 + 1e-7))
+
+
+def test_i8_round_trip_bound():
+    psi = sy.complex_normal(1961, (50, 4, 4, 3)) * np.geomspace(1e-3, 1e3, 4)[None, :, None, None]
+    scale, q = encode_i8(psi)
+    assert scale.dtype == np.float16 and q.dtype == np.int8 and q.shape == (50, 4, 24)
+    out = decode_i8(scale, q)
+    v = psi.view(np.float64).reshape(50, 4, 24)
+    w = out.view(np.float64).reshape(50, 4, 24)
+    s = np.abs(v).max(axis=-1)
+    sh = scale.astype(np.float64)
+    # half a quantum of the prefactor, plus the prefactor's own FP16 rounding
+    bound = sh / 254.0 + np.abs(s - sh) + 1e-15 * s
+    assert np.all(np.abs(v - w) <= bound[..., None])
+    assert np.all(np.abs(q) <= 127)
+    assert bytes_i8_per_site() == 26
+
+
+def test_i8_zero_and_exact_values():
+    z = np.zeros((3, 2, 4, 3), dtype=np.complex128)
+    sc, q = encode_i8(z)
+    assert np.all(decode_i8(sc, q) == 0)
+    k = np.zeros((1, 1, 4, 3), dtype=np.complex128)
+    k[0, 0, 0, 0] = 2.0
+    k[0, 0, 1, 1] = -1.0j
+    sc, q = encode_i8(k)
+    out = decode_i8(sc, q)
+    assert out[0, 0, 0, 0] == 2.0 and abs(out[0, 0, 1, 1] + 1.0j) < 2.0 / 254
+
+
+@pytest.fixture(scope="module")
+def two_level():
+    dims, Ls = (8, 8, 4, 4), 4
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.05, sy.gauge_field(dims, 0.4, 1962))
+    bl = Blocking(d, (4, 4, 4, 4))
+    phi = inverse_iteration_subspace(d.mdagm, sy.gaussian_fermions(dims, Ls, 1963, 6), bl, steps=2, tol=1e-3)
+    A = dense_to_stencil(coarse_dense_bruteforce(d.mdagm, phi, bl), bl)
+    b = sy.gaussian_fermion(dims, Ls, 1964)
+    ref = adef2(d.mdagm, b, DeflationSpace(phi, bl, A, coarse_tol=0.04), 1e-8)
+    return d, bl, phi, A, b, ref
+
+
+@pytest.mark.parametrize("codec", ["truncate16", "i8"])
+def test_hdcg_with_compressed_smoother_input(two_level, codec):
+    """M_IRS applied to the codec's image of its input (as if that input had
+    crossed a compressed halo): the outer A-DEF2 still meets the tolerance,
+    within a few iterations of the unrounded solve."""
+    d, bl, phi, A, b, ref = two_level
+
+    def squeeze(r):
+        if codec == "truncate16":
+            return truncate16(r)
+        return decode_i8(*encode_i8(r))
+
+    res = adef2(d.mdagm, b, DeflationSpace(phi, bl, A, coarse_tol=0.04), 1e-8,
+                M=lambda r: mirs(d.mdagm, squeeze(r), 7, 1.0))
+    assert res.true_residual < 2e-8
+    assert res.iterations <= ref.iterations + 3
