@@ -12,7 +12,10 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                the prefactor is the largest |real| of the site rounded to
                FP16, the integers are round(127 v / prefactor) clipped to
                [-127, 127], and decoding multiplies back by prefactor / 127.
-               26 bytes per site against 48 (FP16) or 96 (FP32).
+               26 bytes per site against 48 (FP16) or 96 (FP32).  The FP16
+               prefactor limits the range: sites whose largest |real| is below
+               about 6e-8 encode as zero, so data must be normalised first
+               (as the library scales the smoother's input to unit RMS).
 
 Parity: pinned by tests/test_oracle_codec.py (the truncation against the bit
 pattern, the 8-bit round-trip bound of half a quantum plus the prefactor's

@@ -38,8 +38,8 @@ def problem():
 @pytest.mark.parametrize("name", METHODS)
 def test_every_method_reaches_the_solution(problem, name):
     d, defl, b, M, xs = problem
-    x, it = generalised_pcg(name, d.mdagm, b, defl, M, 1e-10, maxiter=2000)
-    assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-7, (name, it)
+    x, it = generalised_pcg(name, d.mdagm, b, defl, M, 1e-8, maxiter=2000)
+    assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-5, (name, it)
 
 
 def test_def2_adef2_bnn_iterates_agree(problem):
