@@ -8,19 +8,24 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                Table sloppy's last row.
 * ``encode_i8`` / ``decode_i8``  a four-spinor of one 5D site (24 reals) as
                a half-precision prefactor and 24 signed 8-bit integers (the
-               proposal of Sec. 6.5: "maxabs, divide, and convert").  Reading:
+               proposal of Sec. 6.5: scale by the largest magnitude and round
+               to bytes).  Reading:
                the prefactor is the largest |real| of the site rounded to
                FP16, the integers are round(127 v / prefactor) clipped to
                [-127, 127], and decoding multiplies back by prefactor / 127.
                26 bytes per site against 48 (FP16) or 96 (FP32).  The FP16
-               prefactor limits the range: sites whose largest |real| is below
-               about 6e-8 encode as zero, so data must be normalised first
+               prefactor limits the range: sites whose largest |real| is at
+               most 2^-25 (about 3e-8) encode as zero, those below 2^-14 keep
+               fewer prefactor bits, and 65520 or more gives an infinite
+               prefactor (NaN once decoded), so data must be normalised first
                (as the library scales the smoother's input to unit RMS).
 
 Parity: pinned by tests/test_oracle_codec.py (the truncation against the bit
 pattern, the 8-bit round-trip bound of half a quantum plus the prefactor's
-rounding, exact zeros, the byte count, and an HDCG solve whose M_IRS input
-passes through either codec converging like the unrounded one).
+rounding, the prefactor against the nearest binary16 found by enumerating
+every half (one rounding from double, ties to even, subnormals, overflow),
+exact zeros, the byte count, and an HDCG solve whose M_IRS input passes
+through either codec converging like the unrounded one).
 """
 from __future__ import annotations
 

@@ -26,10 +26,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def _env() -> dict:
+    # nvcc's intermediate files go to the build folder, not the system temporary directory
+    return {**os.environ, "TMPDIR": BUILD}
+
+
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
     cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=_env())
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr[-4000:]}")
     return obj
@@ -52,7 +57,7 @@ def build(force: bool = False, verbose: bool = True) -> str:
         objs = list(ex.map(_compile, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=_env())
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
     os.replace(tmp, LIB)

@@ -82,3 +82,29 @@ def test_hdcg_with_compressed_smoother_input(two_level, codec):
                 M=lambda r: mirs(d.mdagm, squeeze(r), 7, 1.0))
     assert res.true_residual < 2e-8
     assert res.iterations <= ref.iterations + 3
+
+
+def _half_by_enumeration(x):
+    """The binary16 value nearest to x >= 0 (ties to the even bit pattern), by
+    search over every finite non-negative half; +inf at or beyond 65520."""
+    bits = np.arange(0, 0x7C00, dtype=np.uint16)
+    vals = bits.view(np.float16).astype(np.float64)
+    if x >= 65520.0:
+        return np.uint16(0x7C00)
+    d = np.abs(vals - x)
+    cand = np.flatnonzero(d == d.min())
+    even = [c for c in cand if bits[c] % 2 == 0]
+    return bits[even[0] if len(cand) > 1 else cand[0]]
+
+
+def test_i8_prefactor_is_the_correctly_rounded_half():
+    """The prefactor rounds max |v| from double to binary16 directly (one
+    rounding): a value just above a midpoint that a float32 step would move
+    onto the midpoint, subnormal ties, and the overflow edge."""
+    xs = [1 + 2.0 ** -11 + 2.0 ** -40, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 2.0 ** -25, 3 * 2.0 ** -25,
+          2.0 ** -25 * (1 + 2.0 ** -30), 6.1e-5, 65519.0, 65504.0, 65519.99, 0.3, 1e-7]
+    for x in xs:
+        psi = np.zeros((1, 4, 3), dtype=np.complex128)
+        psi[0, 0, 0] = x
+        scale, _ = encode_i8(psi)
+        assert scale.view(np.uint16)[0] == _half_by_enumeration(x), x
