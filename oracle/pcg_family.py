@@ -8,22 +8,33 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                alpha = (r, y)/(p, w), x += alpha p, r -= alpha w, y = M_1 r,
                beta = (r_new, y_new)/(r, y) (or the flexible form), p = M_2 y +
                beta p; x = V_end.
-* ``METHODS``  Table algos: PREC, AD, DEF1, DEF2, A-DEF1, A-DEF2, BNN and the
-               Hermitian V(1,1) multigrid cycle, built from Q = P A^-1 R and a
-               smoother M, with P_L = 1 - H Q and P_R = 1 - Q H.
+* ``METHODS``  Table algos: PREC, AD, DEF1, DEF2, A-DEF1, A-DEF2, BNN, the
+               Hermitian V(1,1) multigrid cycle and MssDef, built from
+               Q = P A^-1 R and a smoother M, with P_L = 1 - H Q and
+               P_R = 1 - Q H.
                Readings: (i) DEF1 (M_3 = P_L) iterates on the deflated system
                P_L H x = P_L b, so its start residual is P_L (b - H x_0); with
                the unprojected residual of the figure the recursion could not
                reach zero.  (ii) A-DEF1 takes M_2 = 1 (the table prints P_R;
                see ``solvers.adef1``).  (iii) BNN may start from x or from the
                DEF2 start Q b + P_R x ("appropriate start vectors", Sec. 4.5).
+               (iv) MssDef, the little Dirac operator as the only
+               preconditioner with no smoother, is A-DEF2 with M = 1:
+               V_start = Q b + P_R x and M_1 = P_R + Q.
+* ``ChebyshevSmoother``  the Chebyshev option of Table preconditioner: the
+               order-n Chebyshev approximation to H^-1 on [lo, hi]
+               (``solvers.chebyshev_inverse`` with H in place of Q_trunc), a
+               fixed polynomial in H, so linear and Hermitian.
 * ``MirsPoly``  M_IRSpoly (Table preconditioner): the CG polynomial of a fixed
                number of iterations on H + lambda, frozen from one CG pass on a
                reference vector (its alpha_k and beta_k) and replayed on any
                vector, so it is a fixed linear, Hermitian operator.
 
 Parity: pinned by tests/test_oracle_pcg_family.py (every method reaches the
-CG solution; with exact Q and a linear smoother DEF2, A-DEF2 and BNN from the
+CG solution; MssDef iterates as DEF2 with M = 1 (the same equivalence);
+A-DEF2 with the Chebyshev smoother reaches it too, and that smoother is the
+polynomial of its eigenvalues (checked on a dense Hermitian matrix) and
+Hermitian; with exact Q and a linear smoother DEF2, A-DEF2 and BNN from the
 DEF2 start produce the same iterates, and DEF1's V_end the same solution, as
 the equivalence of Sec. 4.5 states; the V(1,1) and BNN preconditioners are
 Hermitian; M_IRSpoly reproduces M_IRS on its reference vector and is linear
@@ -33,7 +44,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .solvers import DeflationSpace
+from .solvers import DeflationSpace, chebyshev_inverse
 
 
 def _dot(a, b):
@@ -74,6 +85,17 @@ class MirsPoly:
             r = r - a * (self.apply_H(p) + self.shift * p)
             p = r + bt * p
         return x
+
+
+class ChebyshevSmoother:
+    """p(H): order ``order`` (PreconditionerKrylovIterMax) on [lo, hi]
+    (PreconditionerKrylovLo, PreconditionerKrylovHi)."""
+
+    def __init__(self, apply_H, order: int, lo: float, hi: float):
+        self.apply_H, self.order, self.lo, self.hi = apply_H, order, lo, hi
+
+    def __call__(self, v):
+        return chebyshev_inverse(self.apply_H, v, self.order, self.lo, self.hi)
 
 
 def _ops(apply_H, defl: DeflationSpace, M):
@@ -121,6 +143,8 @@ def method(name: str, apply_H, defl: DeflationSpace, M):
         return start_x, lambda r: PR(M(PL(r))) + Q(r), ident, ident, end_x, False
     if name == "BNN-DEF2-start":
         return start_def2, lambda r: PR(M(PL(r))) + Q(r), ident, ident, end_x, False
+    if name == "MssDef":
+        return start_def2, lambda r: PR(r) + Q(r), ident, ident, end_x, False
     if name == "V11":
         def m1(r):
             mr = M(r)
@@ -129,7 +153,7 @@ def method(name: str, apply_H, defl: DeflationSpace, M):
     raise ValueError(f"unknown method {name}")
 
 
-METHODS = ("PREC", "AD", "DEF1", "DEF2", "A-DEF1", "A-DEF2", "BNN", "BNN-DEF2-start", "V11")
+METHODS = ("PREC", "AD", "DEF1", "DEF2", "A-DEF1", "A-DEF2", "BNN", "BNN-DEF2-start", "V11", "MssDef")
 
 
 def generalised_pcg(name: str, apply_H, b, defl: DeflationSpace, M, tol: float, maxiter: int = 10000,

@@ -17,7 +17,7 @@ import pytest
 import synthetic as sy
 from oracle.coarse import Blocking, coarse_dense_bruteforce, dense_to_stencil
 from oracle.dwf import DWF, norm2
-from oracle.pcg_family import METHODS, MirsPoly, generalised_pcg, method
+from oracle.pcg_family import METHODS, ChebyshevSmoother, MirsPoly, generalised_pcg, method
 from oracle.solvers import DeflationSpace, cg, inverse_iteration_subspace, mirs
 
 
@@ -84,3 +84,48 @@ def test_mirs_poly_replays_and_is_linear_hermitian(problem):
     assert abs(a - c) < 1e-12 * abs(a)
     # M_IRS itself is not linear: a CG polynomial adapts to its right-hand side
     assert np.abs(mirs(d.mdagm, u + v, 6, 1.0) - mirs(d.mdagm, u, 6, 1.0) - mirs(d.mdagm, v, 6, 1.0)).max() > 1e-6
+
+
+def test_mssdef_is_def2_without_a_smoother(problem):
+    """MssDef (the little Dirac operator alone) iterates as DEF2 with M = 1,
+    by the same equivalence with exact Q, and reaches the solution in more
+    iterations than with the smoother."""
+    d, defl, b, M, xs = problem
+    ident = lambda v: v
+    h1, h2 = [], []
+    x1, it1 = generalised_pcg("MssDef", d.mdagm, b, defl, M, 1e-10, maxiter=3000, history=h1)
+    x2, it2 = generalised_pcg("DEF2", d.mdagm, b, defl, ident, 1e-10, maxiter=3000, history=h2)
+    assert abs(it1 - it2) <= 2
+    for k, (a, c) in enumerate(zip(h1[:15], h2[:15])):
+        assert np.sqrt(norm2(a - c) / norm2(xs)) < 1e-9, k
+    _, it_smoothed = generalised_pcg("A-DEF2", d.mdagm, b, defl, M, 1e-10, maxiter=3000)
+    assert it_smoothed < it1
+
+
+def _lambda_max(d, seed, iters=30):
+    v = sy.gaussian_fermion(d.lat.dims, d.Ls, seed)
+    lam = 0.0
+    for _ in range(iters):
+        v = v / np.sqrt(norm2(v))
+        w = d.mdagm(v)
+        lam = float(np.vdot(v, w).real)
+        v = w
+    return lam
+
+
+def test_chebyshev_smoother(problem):
+    """The Chebyshev option of Table preconditioner (order 8 on [hi/90, hi],
+    hi above the spectrum): linear and Hermitian, and A-DEF2 with it reaches
+    the CG solution."""
+    d, defl, b, M, xs = problem
+    hi = 1.2 * _lambda_max(d, 1807)
+    C = ChebyshevSmoother(d.mdagm, 8, hi / 90, hi)
+    u = sy.gaussian_fermion(d.lat.dims, d.Ls, 1808)
+    v = sy.gaussian_fermion(d.lat.dims, d.Ls, 1809)
+    lin = C(2.0 * u - 0.5j * v) - (2.0 * C(u) - 0.5j * C(v))
+    assert np.abs(lin).max() < 1e-12 * np.abs(C(u)).max()
+    a, c = np.vdot(u, C(v)), np.vdot(C(u), v)
+    assert abs(a - c) < 1e-12 * abs(a)
+    assert np.vdot(u, C(u)).real > 0
+    x, it = generalised_pcg("A-DEF2", d.mdagm, b, defl, C, 1e-8, maxiter=2000)
+    assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-5, it
