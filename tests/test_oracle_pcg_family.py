@@ -129,3 +129,19 @@ def test_chebyshev_smoother(problem):
     assert np.vdot(u, C(u)).real > 0
     x, it = generalised_pcg("A-DEF2", d.mdagm, b, defl, C, 1e-8, maxiter=2000)
     assert np.sqrt(norm2(x - xs) / norm2(xs)) < 1e-5, it
+
+
+def test_prec_with_identity_is_textbook_cg(problem):
+    """With M = 1 the generalised PCG of Fig. pcg_general reduces to the
+    textbook CG: the same residual norms iteration by iteration (recomputed
+    from its iterates) and the same iteration count."""
+    d, defl, b, M, xs = problem
+    hist_x, hist_r = [], []
+    x1, it1 = generalised_pcg("PREC", d.mdagm, b, defl, lambda v: v, 1e-8, flexible=False, history=hist_x)
+    x2, it2 = cg(d.mdagm, b, 1e-8, history=hist_r)
+    assert abs(it1 - it2) <= 1
+    bn = np.sqrt(norm2(b))
+    for k, (xk, rk) in enumerate(zip(hist_x[:30], hist_r[:30])):
+        tr = np.sqrt(norm2(b - d.mdagm(xk))) / bn
+        assert abs(tr - rk) <= 1e-6 * rk, k
+    assert np.sqrt(norm2(x1 - x2) / norm2(x2)) < 1e-8
