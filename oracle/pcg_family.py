@@ -17,7 +17,8 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                the unprojected residual of the figure the recursion could not
                reach zero.  (ii) A-DEF1 takes M_2 = 1 (the table prints P_R;
                see ``solvers.adef1``).  (iii) BNN may start from x or from the
-               DEF2 start Q b + P_R x ("appropriate start vectors", Sec. 4.5).
+               DEF2 start Q b + P_R x (the equivalence of Sec. 4.5 holds for
+               suitably chosen start vectors).
                (iv) MssDef, the little Dirac operator as the only
                preconditioner with no smoother, is A-DEF2 with M = 1:
                V_start = Q b + P_R x and M_1 = P_R + Q.

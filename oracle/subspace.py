@@ -19,21 +19,21 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                to normalisation, and the block Gram-Schmidt removes it).
 * ``wall_noise``  4D Gaussian noise on the physical components of the walls,
                P_- psi(s = 0) and P_+ psi(s = Ls - 1): the components that the
-               mass term of P_s couples (reading of "the physical field
-               components of the walls").
+               mass term of P_s couples (our reading of where Sec. 4.2 puts
+               the noise).
 * ``surface_truncate``  SubspaceSurfaceDepth: the s-slices farther than
                ``depth`` from both walls set to zero.
 * ``rational_subspace``  wall noise, the filter, block Gram-Schmidt.
 * ``promote``  a field of a reduced fifth dimension Ls1 placed into Ls: the
                half of the s-slices nearer each wall keeps its distance to that
-               wall, the bulk between is zero ("promoted to the surface regions
-               of the full system").
+               wall, the bulk between is zero (our reading of the promotion to
+               the full system's surfaces in Sec. 4.2).
 * ``two_pass_subspace``  the two-stage generation (Sec. 4.2, Table optimised,
                first and second pass controls): the filter on a reduced-Ls
                operator with its own mass, promotion, then one shifted inversion
                (H + lam2)^-1 of every promoted vector on the full system by
-               A-DEF2 deflated with the promoted vectors (the "first pass
-               deflated solver"), to a loose residual, and block Gram-Schmidt.
+               A-DEF2 deflated with the promoted vectors (the solver that the
+               first pass provides), to a loose residual, and block Gram-Schmidt.
                Reading: the deflation space of the second pass is the block
                Gram-Schmidt of the promoted vectors, its coarse operator that of
                H + lam2 (A + lam2 on the diagonal blocks, exact for orthonormal
