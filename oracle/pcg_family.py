@@ -32,7 +32,8 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                vector, so it is a fixed linear, Hermitian operator.
 
 Parity: pinned by tests/test_oracle_pcg_family.py (PREC with M = 1 is the
-textbook CG, residual by residual; every method reaches the CG solution; MssDef iterates as DEF2 with M = 1 (the same equivalence);
+textbook CG, residual by residual; each M_1 equals its form as smoothing and
+coarse-correction steps, V(1,1) the symmetric two-grid cycle; every method reaches the CG solution; MssDef iterates as DEF2 with M = 1 (the same equivalence);
 A-DEF2 with the Chebyshev smoother reaches it too, and that smoother is the
 polynomial of its eigenvalues (checked on a dense Hermitian matrix) and
 Hermitian; with exact Q and a linear smoother DEF2, A-DEF2 and BNN from the

@@ -145,3 +145,38 @@ def test_prec_with_identity_is_textbook_cg(problem):
         tr = np.sqrt(norm2(b - d.mdagm(xk))) / bn
         assert abs(tr - rk) <= 1e-6 * rk, k
     assert np.sqrt(norm2(x1 - x2) / norm2(x2)) < 1e-8
+
+
+def _steps(name, H, Q, M, r):
+    """M1 r as the sequence of smoothing and coarse-correction steps."""
+    if name == "V11":                       # pre-smooth, coarse-correct, post-smooth
+        z = M(r)
+        z = z + Q(r - H(z))
+        return z + M(r - H(z))
+    if name == "BNN":                       # z = M (r - H Q r), then coarse-correct
+        z = M(r - H(Q(r)))
+        return z + Q(r - H(z))
+    if name == "A-DEF1":                    # coarse-correct, then smooth the rest
+        q = Q(r)
+        return q + M(r - H(q))
+    if name == "A-DEF2":                    # smooth, then coarse-correct
+        z = M(r)
+        return z + Q(r - H(z))
+    if name == "AD":
+        return M(r) + Q(r)
+    if name == "MssDef":                    # coarse correction of r itself
+        return r + Q(r - H(r))
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name", ["V11", "BNN", "A-DEF1", "A-DEF2", "AD", "MssDef"])
+def test_preconditioners_as_smoothing_and_coarse_steps(problem, name):
+    """Each M_1 of Tables precs and algos, written with P_L = 1 - H Q and
+    P_R = 1 - Q H, equals its form as smoothing and coarse-correction steps
+    (V(1,1): the symmetric two-grid cycle)."""
+    d, defl, b, M, xs = problem
+    M1 = method(name, d.mdagm, defl, M)[1]
+    r = sy.gaussian_fermion(d.lat.dims, d.Ls, 1810)
+    want = M1(r)
+    got = _steps(name, d.mdagm, defl.Q, M, r)
+    assert np.abs(got - want).max() < 1e-10 * np.abs(want).max()
