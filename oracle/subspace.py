@@ -43,6 +43,7 @@ Parity: pinned by tests/test_oracle_subspace.py (the partial fractions
 against the product at sample points; multi-shift solutions against numpy's
 dense solves and, for one shift, against the textbook CG iterate by iterate;
 the filter against the eigendecomposition of a dense Hermitian matrix; the
+coarse operator of H + lam2 against its brute-force assembly; the
 support and chirality of the wall noise; the truncation; the filtered
 subspace of a domain wall operator concentrating on its low modes; the
 promotion's placement; the two-pass result solving its shifted systems, equal

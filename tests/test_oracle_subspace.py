@@ -159,3 +159,18 @@ def test_two_pass_refined_subspace(dwf8):
     assert q_phi < 0.1 * q_gauss
     w = np.sqrt((np.abs(phi) ** 2).sum(axis=(1, 3, 4)))   # (nvec, Ls) weight per s-slice
     assert np.all(w[:, [0, -1]].sum(axis=1) > w[:, 2:4].sum(axis=1))
+
+
+def test_second_pass_coarse_operator_is_shifted_by_lam2():
+    """The reading behind the second pass: for block-orthonormal vectors the
+    coarse operator of H + lam2 is that of H plus lam2 on the diagonal blocks
+    (P^dag P = 1), which is how the second pass builds it."""
+    from oracle.coarse import block_gram_schmidt, coarse_dense_bruteforce
+    dims, Ls, lam2 = (8, 4, 4, 4), 4, 1e-3
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.02, sy.gauge_field(dims, 0.4, 1717))
+    bl = Blocking(d, (4, 4, 4, 4))
+    basis = block_gram_schmidt(sy.gaussian_fermions(dims, Ls, 1718, 3), bl)
+    A = coarse_dense_bruteforce(d.mdagm, basis, bl)
+    As = coarse_dense_bruteforce(lambda v: d.mdagm(v) + lam2 * v, basis, bl)
+    eye = np.einsum("ab,jk->ajbk", np.eye(bl.Vc), np.eye(3))
+    assert np.abs(As - (A + lam2 * eye)).max() < 1e-12 * np.abs(A).max()
