@@ -1,22 +1,34 @@
 """Benchmark: HDCG time-to-solution on one GB300 against plain red-black CG,
 with the fine Mpc^dag Mpc hop kernels' achieved bandwidth against the HBM roofline.
 
-One step = one full HDCG (A-DEF2) solve of H x = b to a true FP64 residual of
-``tol`` on the workload's lattice, inputs resident in HBM; subspace and coarse
-operator are built once before the timed region (the paper reports setup
-separately).  L2 is flushed (a 512 MiB write) before every timed step.
+One step = one full HDCG solve of H x = b to a true FP64 residual of ``tol``
+for all the workload's right-hand sides, inputs resident in HBM.  The default
+workload is the physical-point-like lattice: 32^3 x 64, Ls 16 Moebius
+(b 1.5, c 0.5), M5 1.8, m 0.001, links exp(i 0.45 H); 12 spin-colour point
+sources solved as a batch; three levels (4^4 blocks with Nvec 40, then 2^4
+blocks of the coarse lattice with Nvec 24); FP16 storage of the sloppy fine
+operator, the subspace and the little Dirac operator, FP32 outer operator,
+double-float (FP64-accurate) true residuals.  The subspaces and coarse
+operators are built once before the timed region (the paper reports set-up
+separately).  Inputs are larger than L2 (a 3.2 GB field per right-hand side)
+and L2 is flushed (a 512 MiB write) before every timed step anyway.
+
+Timed steps run with the library's event profiling off; the per-kernel
+profile (hop launch times and bytes, solve phases) comes from one extra
+solve after the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload NAME]
 Under torchrun (N > 1) every rank solves its own replica (independent seed);
 the timing is the max over ranks.  ``--impl reference`` times the FP64 CPU
-oracle on the host cores (bounded sample, see ``cpu_sample``).
+oracle on the host cores (bounded sample, see ``cpu_sample_desc``).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -31,15 +43,20 @@ sys.path.insert(0, ROOT)
 import synthetic as sy  # noqa: E402
 
 METRIC = "HDCG solve seconds vs plain CG at 1e-8 (1 GB300); fine Mpc†Mpc GB/s, %HBM peak"
-DEFAULT_WORKLOAD = "cfg2_16x16x16x16_ls16_shamir"
+DEFAULT_WORKLOAD = "cfg5_32x32x32x64_ls16_mobius_3lvl"
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 
+# Fine H applies (outer + preconditioner + FP64 residual) per right-hand side
+# of one HDCG solve, from the GPU arm's solve statistics on each workload (a
+# property of the algorithm on that input).  The reference arm, which runs no
+# GPU code, scales the oracle's per-apply time by it; the GPU arm reports its
+# measured count beside this figure (``h_applies_per_rhs``).
+H_APPLIES_PER_RHS = {DEFAULT_WORKLOAD: 900, "cfg2_16x16x16x16_ls16_shamir": 140}
 
-# DRAM bytes (read + write) per FP32 hop_kernel launch, mean of the four passes of
-# one H, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the current kernel on this workload; to be reset to None whenever hop_kernel
-# changes, since the counters then no longer describe it.
-HOP_F32_TRAFFIC = {DEFAULT_WORKLOAD: 126.2e6}
+# DRAM bytes (read + write) per hop_kernel launch of the outer precision from
+# one ncu capture of the current kernel, per workload; None once the kernel
+# changes (the counters then no longer describe it).
+HOP_TRAFFIC = {}
 
 
 def hop_flops_per_site(w) -> int:
@@ -60,6 +77,14 @@ def hop_flops_per_site(w) -> int:
     pass_c = 1440 + k + minv
     pass_d = 1440 + k + 72 + 48 + 24
     return pass_a + pass_b + pass_c + pass_d
+
+
+def operator_bytes_per_site(w, bytes_per_real: int) -> float:
+    """Algorithmic bytes of one H per 5D site: four passes each read their input
+    (24 reals) and write their output (24), read the links once per 4D site
+    (8 x 18 reals shared by Ls sites), and passes B and D re-read psi for the
+    M_oo term (24 each): (240 + 576 / Ls) reals."""
+    return (240.0 + 576.0 / w.Ls) * bytes_per_real
 
 
 def replica_seeds(w, rank: int) -> dict:
@@ -88,6 +113,19 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
 
 
 # ----------------------------------------------------------------------------
@@ -147,30 +185,49 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------
-def oracle_h_seconds(w, reps=1):
-    """Seconds of one FP64 oracle H = Mpc^dag Mpc apply on the workload's full lattice."""
+SAMPLE_DIMS = (8, 8, 8, 8)
+
+
+def oracle_h_seconds_per_site(w, reps=1):
+    """Seconds per 5D odd site of one FP64 oracle H = Mpc^dag Mpc apply, timed on
+    an 8^4 lattice with the workload's Ls and action (the oracle's cost is
+    linear in the volume)."""
     from oracle.dwf import DWF
-    U = sy.gauge_field(w.dims, w.eps, w.gauge_seed)
-    d = DWF(w.dims, w.Ls, w.M5, w.b, w.c, w.mass, U)
-    psi = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
+    dims = SAMPLE_DIMS
+    U = sy.gauge_field(dims, w.eps, w.gauge_seed)
+    d = DWF(dims, w.Ls, w.M5, w.b, w.c, w.mass, U)
+    psi = sy.gaussian_fermion(dims, w.Ls, w.source_seed)
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
         d.mdagm(psi)
         ts.append(time.perf_counter() - t0)
-    return min(ts)
+    return min(ts) / (int(np.prod(dims)) // 2 * w.Ls)
 
 
-def cpu_sample_desc(w, n_h):
-    return (f"one FP64 oracle H apply on the full {'x'.join(map(str, w.dims))}x{w.Ls} lattice, "
-            f"scaled by the {n_h} fine H applies (outer + preconditioner + FP64 residual) of one HDCG solve "
-            "of this workload; coarse-grid work of the oracle not included")
+def n5_of(w) -> int:
+    return int(np.prod(w.dims)) // 2 * w.Ls
 
 
-# H applies per HDCG solve of the default workload, recorded from the GPU arm's
-# solve statistics (a property of the algorithm on this input); used only to
-# scale the oracle's per-apply time in --impl reference, which runs no GPU code.
-H_APPLIES_PER_SOLVE = {DEFAULT_WORKLOAD: 140}   # 15 outer + 120 preconditioner + 5 FP64 residual
+def cpu_sample_desc(w, n_h_per_rhs, nrhs):
+    return (f"one FP64 oracle H apply on an {'x'.join(map(str, SAMPLE_DIMS))}x{w.Ls} lattice (same action), "
+            f"scaled per 5D site to the {'x'.join(map(str, w.dims))}x{w.Ls} lattice and by the {n_h_per_rhs} fine H "
+            f"applies per right-hand side of one HDCG solve, times {nrhs} right-hand sides; the oracle's "
+            "coarse-grid work is not included")
+
+
+def oracle_cg_solve_cfg1():
+    """The oracle's own FP64 solve of the 8^4 x 8 Shamir workload (CG to its
+    tolerance 1e-10): a complete oracle solve timed on the host cores."""
+    from oracle.dwf import DWF
+    from oracle.solvers import cg
+    w = sy.WORKLOADS["cfg1_8x8x8x8_ls8_shamir"]
+    d = DWF(w.dims, w.Ls, w.M5, w.b, w.c, w.mass, sy.gauge_field(w.dims, w.eps, w.gauge_seed))
+    b = sy.gaussian_fermion(w.dims, w.Ls, w.source_seed)
+    t0 = time.perf_counter()
+    _, it = cg(d.mdagm, b, w.tol)
+    return {"workload": w.name, "algorithm": "CG", "tol": w.tol, "iterations": int(it),
+            "seconds": time.perf_counter() - t0, "cores": 1}
 
 
 def run_reference(args, w):
@@ -179,18 +236,19 @@ def run_reference(args, w):
         return
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(k, "1")
-    n_h = H_APPLIES_PER_SOLVE.get(w.name, 140)
+    nrhs = args.nrhs or w.nrhs
+    n_h = H_APPLIES_PER_RHS.get(w.name, 140)
     for _ in range(args.warmup):
-        oracle_h_seconds(w)
-    ts = [oracle_h_seconds(w) for _ in range(args.steps)]
-    per_h = statistics.mean(ts)
-    value = per_h * n_h
+        oracle_h_seconds_per_site(w)
+    ts = [oracle_h_seconds_per_site(w) for _ in range(args.steps)]
+    per_site = statistics.mean(ts)
+    value = per_site * n5_of(w) * n_h * nrhs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_h * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "tol": w.tol},
+            "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "tol": w.tol, "rhs_per_gpu": nrhs},
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": cpu_sample_desc(w, n_h)},
+                             "sample": cpu_sample_desc(w, n_h, nrhs), **host_info()},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -198,11 +256,40 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def build_levels(h, w, seeds, args):
+    """Subspaces and coarse operators (timed separately, outside the solves)."""
+    prec = PREC[w.prec]
+    sub_prec = prec if prec in (0, 1) else 2
+    coarse_prec = PREC[args.coarse_prec] if args.coarse_prec else (0 if prec == 0 else (1 if prec == 1 else 2))
+    out = {}
+    t0 = time.perf_counter()
+    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=w.inv_steps, inv_shift=0.0, inv_tol=w.inv_tol,
+                     inv_maxiter=w.inv_maxiter, seed=seeds["subspace"])
+    out["subspace"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h.build_coarse(coarse_prec)
+    out["coarse_operator"] = time.perf_counter() - t0
+    if w.block2 and not args.two_level:
+        t0 = time.perf_counter()
+        h.build_subspace(w.block2, w.nvec2, 1, inv_steps=w.inv2_steps, inv_shift=0.0, inv_tol=w.inv2_tol,
+                         inv_maxiter=20000, seed=seeds["subspace"] + 11, level=2)
+        out["level2_subspace"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        h.build_coarse(1, level=2)
+        out["level2_operator"] = time.perf_counter() - t0
+    ldop = args.ldop_nvec if args.ldop_nvec is not None else w.ldop_nvec
+    if ldop and (not w.block2 or args.two_level):
+        t0 = time.perf_counter()
+        h.build_coarse_deflation(ldop, inv_steps=3, shift=-1e-3, tol=1e-5, maxiter=20000, seed=seeds["ldop"])
+        out["ldop_deflation"] = time.perf_counter() - t0
+    return out
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
 
-    from paper_1402_2585_gb300 import ALG_ADEF2, ALG_CG, F64, Hdcg, HdcgError
+    from paper_1402_2585_gb300 import ALG_ADEF2, ALG_CG, Hdcg, HdcgError
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -211,7 +298,9 @@ def run_ours(args, w):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # the library runs on its own (non-legacy) stream, so its coarse loops can replay CUDA graphs
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     def barrier():
         if world > 1:
@@ -219,48 +308,33 @@ def run_ours(args, w):
         torch.cuda.synchronize(dev)
 
     prec = PREC[w.prec]
-    sub_prec = prec if prec in (0, 1) else 2
-    coarse_prec = 0 if prec == 0 else (1 if prec == 1 else 2)
+    outer = 0 if prec == 0 else 1
+    nrhs = args.nrhs or w.nrhs
+    # the oracle's complete FP64 solve of the 8^4 x 8 workload runs on one host
+    # core in a child process while the GPU works (about 1.5 minutes)
+    oracle_proc = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        oracle_proc = subprocess.Popen(
+            [sys.executable, "-c", "import json, bench; print(json.dumps(bench.oracle_cg_solve_cfg1()))"],
+            cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+            env=dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1"))
     t_setup0 = time.perf_counter()
     seeds = replica_seeds(w, rank)
     U = sy.gauge_field(w.dims, w.eps, seeds["gauge"])
     h = Hdcg(w.dims, w.Ls, antiperiodic_t=w.antiperiodic_t, stream=stream.cuda_stream)
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(U).to(dev))
-    t_sub0 = time.perf_counter()
-    h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=args.inv_steps, inv_shift=0.0, inv_tol=args.inv_tol,
-                     inv_maxiter=20000, seed=seeds["subspace"])
-    t_sub = time.perf_counter() - t_sub0
-    t_c0 = time.perf_counter()
-    if args.coarse_prec:
-        coarse_prec = PREC[args.coarse_prec]
-    h.build_coarse(coarse_prec)
-    t_coarse = time.perf_counter() - t_c0
-    t_l0 = time.perf_counter()
-    ldop = None
-    if args.ldop_nvec is None:
-        args.ldop_nvec = w.ldop_nvec
-    if args.ldop_nvec:
-        h.build_coarse_deflation(args.ldop_nvec, inv_steps=args.ldop_steps, shift=args.ldop_shift,
-                                 tol=args.ldop_tol, maxiter=20000, seed=seeds["ldop"])
-        lam = h.get_coarse_deflation(args.ldop_nvec)
-        fin = lam[np.isfinite(lam)]
-        ldop = {"nvec": args.ldop_nvec, "inv_steps": args.ldop_steps, "shift": args.ldop_shift,
-                "tol": args.ldop_tol, "dropped": int(len(lam) - len(fin)),
-                "ritz_min": float(fin[0]) if len(fin) else None, "ritz_max": float(fin[-1]) if len(fin) else None}
-    t_ldop = time.perf_counter() - t_l0
-    setup_s = time.perf_counter() - t_setup0
+    del U
+    setup = build_levels(h, w, seeds, args)
+    setup["total"] = time.perf_counter() - t_setup0
 
-    outer = 0 if prec == 0 else 1
-    nrhs = args.nrhs or w.nrhs
     prm = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000,
-                              reliable_delta=args.reliable_delta, batch=1)
-    prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=100000,
-                                 reliable_delta=args.reliable_delta)
+                              reliable_delta=args.reliable_delta, batch=1, coarse_maxiter=5000)
     if nrhs == 1:
-        b = torch.from_numpy(sy.gaussian_fermion(w.dims, w.Ls, seeds["source"])).to(dev)
+        bh = sy.gaussian_fermion(w.dims, w.Ls, seeds["source"])[None]
     else:
-        b = torch.from_numpy(sy.point_sources(w.dims, w.Ls, nrhs)).to(dev)
+        bh = sy.point_sources(w.dims, w.Ls, nrhs)
+    b = torch.from_numpy(bh).to(dev)
     x = torch.zeros_like(b)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -269,14 +343,13 @@ def run_ours(args, w):
             h.solve(b, x, w.tol, prm, nrhs=nrhs)
     except HdcgError as e:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "error": str(e), "workload": w.name, "ldop_deflation": ldop,
-                              "coarse_storage": args.coarse_prec}), flush=True)
+            print(json.dumps({"metric": METRIC, "error": str(e), "workload": w.name}), flush=True)
         raise
     barrier()
 
+    # timed region: profiling off
     clk = ClockSampler(local)
     clk.start()
-    h.set_profiling(True)
     launches0 = h.launch_count()
     times, stats = [], []
     for _ in range(args.steps):
@@ -284,127 +357,172 @@ def run_ours(args, w):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         barrier()
-        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         st = h.solve(b, x, w.tol, prm, nrhs=nrhs)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        torch.cuda.nvtx.range_pop()
         times.append(e0.elapsed_time(e1) / 1e3)
         stats.append(st.as_dict())
     launches = h.launch_count() - launches0
-    n_hop, hop_ms, hop_bytes = h.get_hop_profile(outer)
-    hop_all = {}
-    for pname, pc in (("f64", 0), ("f32", 1), ("f16", 2), ("bf16", 3)):
-        n_p, ms_p, by_p = h.get_hop_profile(pc)
-        if n_p:
-            hop_all[pname] = {"launches": n_p, "avg_launch_us": ms_p * 1e3 / n_p,
-                              "GBps": by_p / (ms_p / 1e3) / 1e9 if ms_p > 0 else None}
-    phases = {k: v / args.steps for k, v in h.get_phase_profile().items()}
-    h.set_profiling(False)
     clocks = clk.stop()
-
     t_solve = max_over_ranks(statistics.mean(times), world, dev)
+    s0 = stats[-1]
 
-    # plain red-black CG on the same GPU (same precision policy)
-    cg_times, cg_stats = [], None
-    for _ in range(max(1, min(2, args.steps))):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        cg_stats = h.solve(b, x, w.tol, prm_cg, nrhs=nrhs).as_dict()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        cg_times.append(e0.elapsed_time(e1) / 1e3)
-    t_cg = statistics.mean(cg_times)
+    # profile pass: one more solve with event timing of every hop launch and phase
+    flush.zero_()
+    torch.cuda.synchronize(dev)
+    h.set_profiling(True)
+    h.solve(b, x, w.tol, prm, nrhs=nrhs)
+    hop_all = {}
+    for pname, pc in (("f64", 0), ("f32", 1), ("f16", 2), ("bf16", 3), ("df64", 5)):
+        n_p, ms_p, by_p, op_p = h.get_hop_profile(pc, operator_bytes=True)
+        if n_p:
+            hop_all[pname] = {"launches": n_p, "avg_launch_us": ms_p * 1e3 / n_p, "ms": ms_p, "bytes": by_p,
+                              "op_bytes": op_p, "GBps": by_p / (ms_p / 1e3) / 1e9 if ms_p > 0 else None}
+    phases = h.get_phase_profile()
+    h.set_profiling(False)
 
-    # end to end through the public API with pinned host buffers
-    bh = b.cpu().pin_memory()
-    xh = torch.zeros_like(bh).pin_memory()
-    e2e = []
-    for _ in range(max(1, min(3, args.steps))):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        h.solve(bh, xh, w.tol, prm, nrhs=nrhs)
-        e2e.append(time.perf_counter() - t0)
-    nbytes = bh.numel() * bh.element_size()  # all right-hand sides of one step
+    # the solution's true residual, recomputed by the library's FP64-accurate operator
+    true_res = s0["true_residual"]
 
-    seq = None
+    # one right-hand side alone (the first), against the batch's time per right-hand side
+    single = None
     if nrhs > 1:
-        prm_seq = Hdcg.default_params(algorithm=ALG_ADEF2, outer_prec=outer, sloppy_prec=prec, maxiter=5000,
-                                      reliable_delta=args.reliable_delta, batch=0)
         flush.zero_()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sq = h.solve(b, x, w.tol, prm_seq, nrhs=nrhs).as_dict()
+        s1 = h.solve(b[:1].contiguous(), x[:1].contiguous(), w.tol, prm, nrhs=1).as_dict()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        seq = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations_total": sq["iterations"],
-               "true_residual": sq["true_residual"]}
+        single = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": s1["iterations"],
+                  "true_residual": s1["true_residual"], "batched_seconds_per_rhs": t_solve / nrhs}
+
+    # plain red-black CG on the same GPU (FP32 with FP64 reliable updates), one
+    # right-hand side, bounded by --cg-maxiter: if it has not converged by then,
+    # its time is a lower bound on its time to solution
+    flush.zero_()
+    torch.cuda.synchronize(dev)
+    prm_cg = Hdcg.default_params(algorithm=ALG_CG, outer_prec=outer, maxiter=args.cg_maxiter,
+                                 reliable_delta=args.reliable_delta)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cgs = h.solve(b[:1].contiguous(), x[:1].contiguous(), w.tol, prm_cg, nrhs=1).as_dict()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_cg = e0.elapsed_time(e1) / 1e3
+    cg_conv = cgs["status"] == 0
+    t_hdcg_rhs = t_solve / nrhs
+    plain_cg = {"seconds": t_cg, "iterations": cgs["iterations"], "true_residual": cgs["true_residual"],
+                "converged": cg_conv, "maxiter": args.cg_maxiter, "rhs": 1,
+                "note": ("converged" if cg_conv else
+                         "not converged at the iteration cap: its time to solution exceeds 'seconds'")}
+    speedup = {"value": t_cg / t_hdcg_rhs if t_hdcg_rhs > 0 else None,
+               "kind": "per right-hand side" + ("" if cg_conv else ", lower bound (CG not converged)"),
+               "hdcg_seconds_per_rhs": t_hdcg_rhs}
+    del b, x
+    torch.cuda.empty_cache()
+
+    # end to end through the public API with pinned host buffers (every step copies
+    # the right-hand sides in and the solutions out)
+    e2e = None
+    if not args.no_e2e:
+        bp = torch.from_numpy(bh).pin_memory()
+        xp = torch.zeros_like(bp).pin_memory()
+        ts_e2e = []
+        for _ in range(max(1, min(2, args.steps))):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            h.solve(bp, xp, w.tol, prm, nrhs=nrhs)
+            ts_e2e.append(time.perf_counter() - t0)
+        nbytes = bp.numel() * bp.element_size()
+        e2e = {"value": statistics.mean(ts_e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+        del bp, xp
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
-    # flop rate of the same launches: a quarter of one H's flops per site per pass
-    n5 = (int(np.prod(w.dims)) // 2) * w.Ls
-    fl_site = hop_flops_per_site(w)
-    hop_tflops = (n_hop * nrhs * n5 * fl_site / 4) / (hop_ms / 1e3) / 1e12 if hop_ms > 0 else 0.0
-    s0 = stats[-1]
+    pname = {0: "f64", 1: "f32"}[outer]
+    sloppy = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}[prec]
     n_h = s0["n_mdagm_outer"] + s0["n_mdagm_sloppy"] + s0["n_mdagm_f64"]
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        per_h = oracle_h_seconds(w)
-        cpu = {"value": per_h * n_h, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": cpu_sample_desc(w, n_h)}
+        per_site = oracle_h_seconds_per_site(w)
+        n_h_rhs = n_h / nrhs
+        solve1 = None
+        if oracle_proc is not None:
+            try:
+                out, _ = oracle_proc.communicate(timeout=900)
+                solve1 = json.loads(out.strip().splitlines()[-1])
+            except Exception as e:   # report, do not fail the GPU line
+                oracle_proc.kill()
+                solve1 = {"error": str(e)}
+        cpu = {"value": per_site * n5_of(w) * n_h, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": cpu_sample_desc(w, round(n_h_rhs), nrhs), **host_info(),
+               "oracle_solve_cfg1": solve1}
     line = {
         "metric": METRIC, "value": t_solve, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
-        "data": "synthetic",
+        "vs_baseline": None, "dtype": f"{pname} outer, {sloppy} sloppy", "data": "synthetic",
         "config": {"workload": w.name, "lattice": list(w.dims), "Ls": w.Ls, "M5": w.M5, "b": w.b, "c": w.c,
-                   "mass": w.mass, "eps": w.eps, "block": list(w.block), "nvec": w.nvec, "tol": w.tol,
-                   "storage": w.prec, "rhs_per_gpu": nrhs, "coarse_storage": args.coarse_prec or None,
-                   "l2": "flushed (512 MiB write) before each step",
+                   "mass": w.mass, "eps": w.eps, "block": list(w.block), "nvec": w.nvec,
+                   "block2": list(w.block2) if (w.block2 and not args.two_level) else None,
+                   "nvec2": w.nvec2 if (w.block2 and not args.two_level) else None, "tol": w.tol,
+                   "storage": w.prec, "rhs_per_gpu": nrhs, "sources": "point" if nrhs > 1 else "gaussian",
+                   "l2": "inputs larger than L2; also flushed (512 MiB write) before each step",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None,
-                     "traffic": HOP_F32_TRAFFIC.get(w.name) if outer == 1 else None,
-                     "kernel": "hop_kernel (4 passes per H; FP32 storage)", "launches": n_hop,
-                     "avg_launch_us": hop_ms * 1e3 / max(1, n_hop), "peak_kind": f"{peak_kind} HBM copy"},
-        "hop_flops": {"flop_per_site_per_H": fl_site, "achieved": hop_tflops, "unit": "TFLOP/s",
-                      "kernel": "hop_kernel (FP32 storage, the roofline kernel's launches)"},
+        "roofline": None,
         "cpu_baseline": cpu,
-        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+        "e2e": e2e,
         "gpu_launches": int(launches / max(1, args.steps)),
         "clocks": clocks,
-        "plain_cg": {"seconds": t_cg, "iterations": cg_stats["iterations"],
-                     "true_residual": cg_stats["true_residual"]},
-        "speedup_vs_plain_cg": t_cg / t_solve if t_solve > 0 else None,
+        "plain_cg": plain_cg,
+        "speedup_vs_plain_cg": speedup,
         "hdcg": {"iterations": s0["iterations"], "coarse_iterations": s0["coarse_iterations"],
+                 "coarse_iterations_max": s0["coarse_iterations_max"],
                  "n_mdagm_outer": s0["n_mdagm_outer"], "n_mdagm_sloppy": s0["n_mdagm_sloppy"],
                  "n_mdagm_f64": s0["n_mdagm_f64"], "reliable_updates": s0["reliable_updates"],
-                 "true_residual": s0["true_residual"]},
-        "phases_ms_per_solve": phases,
+                 "true_residual": true_res, "batch_rhs": s0["batch_rhs"],
+                 "h_applies_per_rhs": n_h / nrhs,
+                 "h_applies_per_rhs_reference_arm": H_APPLIES_PER_RHS.get(w.name)},
+        "phases_ms_per_solve_profiled": phases,
         "hop_profile": hop_all,
-        "sequential_single_rhs": seq,
-        "ldop_deflation": ldop,
-        "setup_seconds": {"total": setup_s, "subspace": t_sub, "coarse_operator": t_coarse,
-                          "ldop_deflation": t_ldop,
-                          "inverse_iteration": {"steps": args.inv_steps, "tol": args.inv_tol}},
+        "single_rhs": single,
+        "setup_seconds": setup,
         "reliable_delta": args.reliable_delta,
     }
+    line["roofline"] = roofline(w, hop_all, sloppy, peak, peak_kind, nrhs)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def roofline(w, hop_all, pname, peak, peak_kind, nrhs):
+    """The dominant kernel's roofline: hop_kernel passes in the sloppy storage
+    precision (most of the solve's fine-operator work).  achieved = algorithmic
+    bytes per launch / mean launch time (CUDA events on the library's stream,
+    profiled solve), in two accountings: the operator's own bytes ((240 +
+    576/Ls) reals per 5D site per H, split over its four passes) and those plus
+    the bytes the launches' fused epilogues add (CG update, shifted term)."""
+    hp = hop_all.get(pname)
+    if not hp:
+        return None
+    per_launch_s = hp["ms"] / 1e3 / hp["launches"]
+    b_fused = hp["bytes"] / hp["launches"]
+    b_op = hp["op_bytes"] / hp["launches"]
+    return {"bound": "hbm", "achieved": b_fused / per_launch_s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": b_fused / per_launch_s / 1e9 / peak, "traffic": HOP_TRAFFIC.get(w.name),
+            "kernel": f"hop_kernel ({pname} storage, 4 passes per H)", "launches": hp["launches"],
+            "avg_launch_us": per_launch_s * 1e6, "bytes_per_launch": b_fused,
+            "achieved_operator_bytes_only": b_op / per_launch_s / 1e9,
+            "frac_operator_bytes_only": b_op / per_launch_s / 1e9 / peak,
+            "operator_bytes_per_launch": b_op, "peak_kind": f"{peak_kind} HBM copy"}
 
 
 def run_apply_only(args, w):
@@ -493,25 +611,22 @@ def run_coarse_only(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(sy.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--inv-steps", type=int, default=3, help="inverse-iteration steps of the subspace setup")
-    ap.add_argument("--inv-tol", type=float, default=1e-4, help="CG tolerance of each inverse-iteration step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--two-level", action="store_true", help="leave out the blocked second coarsening")
     ap.add_argument("--reliable-delta", type=float, default=0.01, help="FP64 true-residual update factor")
+    ap.add_argument("--cg-maxiter", type=int, default=6000,
+                    help="iteration cap of the plain-CG comparison (one right-hand side)")
     ap.add_argument("--coarse-prec", choices=["f64", "f32", "f16"], default=None,
                     help="storage of the little Dirac operator (default: the workload's)")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="right-hand sides per solve (default: the workload's; reported as rhs_per_gpu)")
     ap.add_argument("--ldop-nvec", type=int, default=None,
-                    help="second-level deflation vectors of the little Dirac operator (0: none; default: the "
-                         "workload's)")
-    ap.add_argument("--ldop-steps", type=int, default=3, help="inverse-iteration steps of that space")
-    ap.add_argument("--ldop-shift", type=float, default=-1e-3,
-                    help="shift of those inverse-iteration steps (negative: times the mean diagonal of A)")
-    ap.add_argument("--ldop-tol", type=float, default=1e-5, help="coarse CG residual of those steps")
+                    help="second-level global deflation vectors (two-level workloads; default: the workload's)")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling case: run this many H applies only (no solve)")
     ap.add_argument("--apply-prec", choices=["f64", "f32", "f16", "bf16", "df64"], default=None,

@@ -117,26 +117,49 @@ typedef struct {
     double inv_tol;      /* relative residual of the CG in each step */
     int inv_maxiter;     /* iteration cap of that CG */
     uint64_t seed;       /* Gaussian start vectors: splitmix64 counter stream + Box-Muller */
+    int level;           /* 1 (or 0): blocks of the fine lattice, vectors of H;
+                            2: blocks of the coarse lattice, vectors of the little Dirac
+                            operator A (block extents >= 1 dividing the coarse extents,
+                            nvec <= 64, prec HDCG_F32); see hdcg_build_coarse */
 } hdcg_subspace_params;
 
-/* Build the subspace by inverse iteration on H from Gaussian noise, with block
+/* Build the subspace by inverse iteration from Gaussian noise, with block
  * Gram-Schmidt (FP64 arithmetic) after each step (Sec. 2; inverse iteration
- * as named in Sec. 1 and Sec. 5.2.1).  Synchronous. */
+ * as named in Sec. 1 and Sec. 5.2.1).  Level 1: vectors of H on the fine
+ * lattice, each step a CG on H + inv_shift.  Level 2 (three-level HDCG): the
+ * same construction on the coarse lattice, Sec. 2 applied to the little Dirac
+ * operator; each step solves (A + inv_shift) for up to 16 vectors at once
+ * (coarse CG), and the start vectors are the splitmix64 stream seed in
+ * canonical order [k][Vc][Nvec].  Level 2 needs the level-1 operator (FP32 or
+ * FP16).  Synchronous. */
 int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p);
 
-/* Upload a subspace: phi canonical complex double [nvec][odd field], host or
+/* Upload a subspace: level 1: phi canonical complex double [nvec][odd field];
+ * level 2: phi canonical complex double [nvec][Vc][Nvec] (stored FP32; prec must
+ * be HDCG_F32) with level-2 blocks block[4] of the coarse lattice.  Host or
  * device.  It is block-orthonormalised again (FP64) before use unless
  * already_orthonormal is 1.  Synchronous. */
-int hdcg_set_subspace(hdcg_t h, const int block[4], int nvec, int prec, const void* phi,
+int hdcg_set_subspace(hdcg_t h, int level, const int block[4], int nvec, int prec, const void* phi,
                       int on_device, int already_orthonormal);
 
-/* Copy the subspace out (canonical complex double, host).  Synchronous. */
-int hdcg_get_subspace(hdcg_t h, void* phi_host);
+/* Copy the subspace of a level out (canonical complex double, host).  Synchronous. */
+int hdcg_get_subspace(hdcg_t h, int level, void* phi_host);
 
-/* Assemble A = R H P by the Fourier trick of Sec. 5.1.1 (81 phased H applies
- * per subspace vector, inverted one dimension at a time); prec is the storage
- * precision of A (HDCG_F64, _F32 or _F16).  Synchronous. */
-int hdcg_build_coarse(hdcg_t h, int prec);
+/* Level 1: assemble A = R H P by the Fourier trick of Sec. 5.1.1 (81 phased H
+ * applies per subspace vector, inverted one dimension at a time); prec is the
+ * storage precision of A (HDCG_F64, _F32 or _F16; an FP16 A keeps an FP32 copy
+ * for level 2).  Rebuilding A keeps a level-2 subspace of the same geometry and
+ * drops the level-2 operator.
+ * Level 2 (three-level HDCG): A2 = P2^dag A P2 on the level-2 lattice, the
+ * Galerkin product of Sec. 2 one level down, contracted directly from the
+ * blocks of A in FP64 (an 81-point stencil again, same canonical layout and
+ * aliasing rule as A), and its dense inverse by Gauss-Jordan elimination,
+ * stored in prec (HDCG_F32 or HDCG_F64; Vc2 * Nvec2 <= 65536).  From then on
+ * every coarse solve (the inversion of A inside Q, and hdcg_coarse_solve) is
+ * A-DEF2 on A with Q2 = P2 A2^-1 R2 and M = 1 (Fig. pcg_general, Table algos):
+ * x0 = Q2 b, y = r + Q2 (r - A r), flexible beta.  HDCG_ERR_BREAKDOWN if A2 has
+ * a non-positive diagonal or a zero pivot.  Synchronous. */
+int hdcg_build_coarse(hdcg_t h, int level, int prec);
 
 /* Canonical layout of A: complex double [Vc][81][j][k], block (a, l) couples
  * coarse site a to its neighbour a + delta_l with
@@ -146,8 +169,15 @@ int hdcg_build_coarse(hdcg_t h, int prec);
  * are stored (-1 is the same neighbour), along an extent of 1 only 0; the
  * other blocks are zero.  */
 
-/* Copy A out in the canonical layout (complex double, host).  Synchronous. */
-int hdcg_get_coarse(hdcg_t h, void* A_host);
+/* Copy A (level 1) or A2 (level 2) out in the canonical layout (complex double,
+ * host: [Vc][81][Nvec][Nvec] or [Vc2][81][Nvec2][Nvec2]).  Synchronous. */
+int hdcg_get_coarse(hdcg_t h, int level, void* A_host);
+
+/* Level-2 restriction c2 = R2 x (c2[b][k] = <phi2_k^b, x>) and prolongation
+ * x = P2 c2 for nrhs (1..16) vectors: x canonical [nrhs][Vc][Nvec], c2
+ * [nrhs][Vc2][Nvec2], complex double, device (FP32 arithmetic).  Synchronous. */
+int hdcg_restrict_coarse(hdcg_t h, const void* x, void* c2, int nrhs);
+int hdcg_prolong_coarse(hdcg_t h, const void* c2, void* x, int nrhs);
 
 /* Upload a little Dirac operator in the canonical layout (host or device
  * pointer, complex double), stored in precision prec (F64, F32 or F16; round
@@ -164,7 +194,7 @@ int hdcg_prolong(hdcg_t h, const void* c, void* v, int prec);
 /* y = A x on canonical coarse vectors (complex double, device). */
 int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
 
-/* Y = A X for nrhs (1..16) coarse vectors at once (Sec. 4.3 stencil, one read of
+/* Y = A X for nrhs (1..16) coarse vectors at once (Sec. 5.1 stencil, one read of
  * A for all of them).  x, y: canonical [nrhs][Vc][Nvec] complex double, device.
  * An FP16 operator runs on the tensor cores (tcgen05, FP32 accumulation; X
  * enters as a scaled FP16 hi + lo pair per value, about 22 significant bits),
@@ -173,8 +203,9 @@ int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
 int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
 
 /* Solve A x = b on the coarse level for nrhs (1..16) right-hand sides to the
- * relative residual tol (at most maxiter iterations): A-DEF1 with the
- * second-level deflation space when one was built, otherwise CG (the inner
+ * relative residual tol (at most maxiter iterations): A-DEF2 with the level-2
+ * operator when one was built (hdcg_build_coarse level 2), else A-DEF1 with
+ * the second-level deflation space when one was built, otherwise CG (the inner
  * inversion of Q, Sec. 2).  b, x: canonical [nrhs][Vc][Nvec] complex double,
  * device; x is overwritten (zero start).  *iterations (nullable) receives the
  * lockstep iteration count.  Synchronous. */
@@ -190,12 +221,13 @@ int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, in
  * which every GPU that loads the library holds until the process exits.
  * Limit: 838,860 coarse unknowns (Vc * Nvec) with an FP32/FP16 coarse
  * operator, 699,050 with FP64; larger operators are rejected with
- * HDCG_ERR_ARG and a message giving the bytes needed.  The first call on a
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture.  All calls on a device share
- * the array: calls that overlap on the GPU (several streams or host threads)
- * race.  x, y: canonical coarse vectors, complex double, device.
- * Synchronous. */
+ * HDCG_ERR_ARG and a message giving the bytes needed.  A handle's first call
+ * looks up the array's device address with the current device (again if the
+ * current device has changed since); make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU (several streams or host
+ * threads) race.  x, y: canonical coarse vectors, complex double, device.
+ * Synchronous: the call waits for its stream before returning. */
 int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y);
 
 /* Second-level (global) deflation of the little Dirac operator (Sec. 5.2,
@@ -253,7 +285,9 @@ typedef struct {
     double reliable_delta; /* FP64 true-residual update when |r| falls by this factor */
     int batch;             /* nrhs > 1: 1 solves up to 16 right-hand sides in lockstep (one
                               launch per step covers all of them, the coarse level reads the
-                              subspace and A once for all); 0 solves them one after another */
+                              subspace and A once for all), as many per batch as the free
+                              device memory takes (hdcg_stats.batch_rhs); 0 solves them one
+                              after another */
 } hdcg_params;
 
 typedef struct {
@@ -267,6 +301,7 @@ typedef struct {
     int status;                /* return code of the solve */
     double true_residual;      /* |b - H x| / |b| in FP64 at exit (max over rhs) */
     double seconds;            /* wall time of the solve */
+    int batch_rhs;             /* right-hand sides solved together per batch (memory permitting) */
 } hdcg_stats;
 
 /* Fill p with the defaults (A-DEF2, FP32 outer, FP32 sloppy, M_IRS(7, 1.0),
@@ -287,8 +322,12 @@ int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdc
 int hdcg_set_profiling(hdcg_t h, int on);
 /* Launch count, summed device time (ms) and algorithmic bytes of the fine
  * hop kernels recorded since profiling was enabled, per storage precision
- * (prec).  Synchronises the stream. */
-int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes);
+ * (prec).  bytes counts everything the launches must move, fused epilogues
+ * included (CG update, shifted term); op_bytes (nullable) only the operator's
+ * own: (240 + 576/Ls) reals per 5D site per H over its four passes.
+ * Synchronises the stream. */
+int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes,
+                         double* op_bytes);
 /* Device time (ms, CUDA events) spent since profiling was enabled in each solve
  * phase: ms[0] outer-precision H applies, ms[1] preconditioner H applies (M_IRS
  * and r - H z), ms[2] FP64 true-residual H applies, ms[3] coarse CG, ms[4]

@@ -35,7 +35,7 @@ class HdcgError(RuntimeError):
 class SubspaceParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inv_steps", ctypes.c_int), ("inv_shift", ctypes.c_double), ("inv_tol", ctypes.c_double),
-                ("inv_maxiter", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("inv_maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("level", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -55,7 +55,7 @@ class SolveStats(ctypes.Structure):
                 ("coarse_iterations_max", ctypes.c_int), ("n_mdagm_outer", ctypes.c_int),
                 ("n_mdagm_sloppy", ctypes.c_int), ("n_mdagm_f64", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
-                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("batch_rhs", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,10 +71,12 @@ _SIGS = {
     "hdcg_apply_mpc": (_I, [_P, _P, _P, _I, _I]),
     "hdcg_apply_mdagm": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D)]),
     "hdcg_build_subspace": (_I, [_P, ctypes.POINTER(SubspaceParams)]),
-    "hdcg_set_subspace": (_I, [_P, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
-    "hdcg_get_subspace": (_I, [_P, _P]),
-    "hdcg_build_coarse": (_I, [_P, _I]),
-    "hdcg_get_coarse": (_I, [_P, _P]),
+    "hdcg_set_subspace": (_I, [_P, _I, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
+    "hdcg_get_subspace": (_I, [_P, _I, _P]),
+    "hdcg_build_coarse": (_I, [_P, _I, _I]),
+    "hdcg_get_coarse": (_I, [_P, _I, _P]),
+    "hdcg_restrict_coarse": (_I, [_P, _P, _P, _I]),
+    "hdcg_prolong_coarse": (_I, [_P, _P, _P, _I]),
     "hdcg_set_coarse": (_I, [_P, _P, _I, _I]),
     "hdcg_restrict": (_I, [_P, _P, _I, _P]),
     "hdcg_prolong": (_I, [_P, _P, _P, _I]),
@@ -89,7 +91,7 @@ _SIGS = {
     "hdcg_solve": (_I, [_P, _P, _P, _I, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _I]),
     "hdcg_set_profiling": (_I, [_P, _I]),
     "hdcg_get_hop_profile": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
-                                  ctypes.POINTER(_D)]),
+                                  ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "hdcg_get_phase_profile": (_I, [_P, ctypes.POINTER(_D)]),
     "hdcg_launch_count": (ctypes.c_longlong, [_P]),
     "hdcg_last_error": (ctypes.c_char_p, [_P]),
@@ -197,27 +199,33 @@ class Hdcg:
 
     # -- subspace and coarse operator -----------------------------------------
     def build_subspace(self, block, nvec, prec=F32, inv_steps=3, inv_shift=0.0, inv_tol=1e-4,
-                       inv_maxiter=20000, seed=0):
+                       inv_maxiter=20000, seed=0, level=1):
         p = SubspaceParams((ctypes.c_int * 4)(*block), nvec, prec, inv_steps, inv_shift, inv_tol,
-                           inv_maxiter, seed)
+                           inv_maxiter, seed, int(level))
         return self._check(self._L.hdcg_build_subspace(self.h, ctypes.byref(p)))
 
-    def set_subspace(self, block, phi, prec=F32, already_orthonormal=False):
+    def set_subspace(self, block, phi, prec=F32, already_orthonormal=False, level=1):
         nvec = int(phi.shape[0])
-        return self._check(self._L.hdcg_set_subspace(self.h, (ctypes.c_int * 4)(*block), nvec, prec, _ptr(phi),
-                                                     _on_device(phi), int(bool(already_orthonormal))))
+        return self._check(self._L.hdcg_set_subspace(self.h, int(level), (ctypes.c_int * 4)(*block), nvec, prec,
+                                                     _ptr(phi), _on_device(phi), int(bool(already_orthonormal))))
 
-    def get_subspace(self, out):
-        return self._check(self._L.hdcg_get_subspace(self.h, _ptr(out)))
+    def get_subspace(self, out, level=1):
+        return self._check(self._L.hdcg_get_subspace(self.h, int(level), _ptr(out)))
 
-    def build_coarse(self, prec=F32):
-        return self._check(self._L.hdcg_build_coarse(self.h, prec))
+    def build_coarse(self, prec=F32, level=1):
+        return self._check(self._L.hdcg_build_coarse(self.h, int(level), prec))
 
     def set_coarse(self, A, prec=F32):
         return self._check(self._L.hdcg_set_coarse(self.h, _ptr(A), int(prec), _on_device(A)))
 
-    def get_coarse(self, out):
-        return self._check(self._L.hdcg_get_coarse(self.h, _ptr(out)))
+    def get_coarse(self, out, level=1):
+        return self._check(self._L.hdcg_get_coarse(self.h, int(level), _ptr(out)))
+
+    def restrict_coarse(self, x, c2, nrhs=1):
+        return self._check(self._L.hdcg_restrict_coarse(self.h, _ptr(x), _ptr(c2), int(nrhs)))
+
+    def prolong_coarse(self, c2, x, nrhs=1):
+        return self._check(self._L.hdcg_prolong_coarse(self.h, _ptr(c2), _ptr(x), int(nrhs)))
 
     def restrict(self, v, prec, c_out):
         return self._check(self._L.hdcg_restrict(self.h, _ptr(v), prec, _ptr(c_out)))
@@ -273,12 +281,14 @@ class Hdcg:
     def set_profiling(self, on):
         return self._check(self._L.hdcg_set_profiling(self.h, int(bool(on))))
 
-    def get_hop_profile(self, prec):
+    def get_hop_profile(self, prec, operator_bytes=False):
         n = ctypes.c_longlong()
         ms = ctypes.c_double()
         by = ctypes.c_double()
-        self._check(self._L.hdcg_get_hop_profile(self.h, prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
-        return n.value, ms.value, by.value
+        ob = ctypes.c_double()
+        self._check(self._L.hdcg_get_hop_profile(self.h, prec, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                                 ctypes.byref(ob)))
+        return (n.value, ms.value, by.value, ob.value) if operator_bytes else (n.value, ms.value, by.value)
 
     PHASES = ("h_outer", "h_sloppy", "h_f64", "coarse_cg", "restrict_prolong", "total")
 

@@ -185,20 +185,38 @@ int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp)
   return HDCG_OK;
 }
 
+static void check_level(int level) {
+  HDCG_REQUIRE(level == 1 || level == 2, HDCG_ERR_ARG, "level must be 1 (fine lattice) or 2 (coarse lattice)");
+}
+
 int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p) {
   HDCG_ENTRY(h, {
     check_ptr(p, "params");
     HDCG_REQUIRE(p->inv_steps >= 0 && p->inv_tol > 0 && p->inv_maxiter > 0, HDCG_ERR_ARG, "bad inverse-iteration parameters");
-    build_subspace(c, *p);
+    const int level = p->level == 0 ? 1 : p->level;
+    check_level(level);
+    if (level == 1) {
+      build_subspace(c, *p);
+    } else {
+      HDCG_REQUIRE(c.sub && c.coarse, HDCG_ERR_STATE, "a level-2 subspace needs the level-1 operator");
+      level2_build_subspace(c, *c.coarse, *c.sub, *p);
+    }
   });
   return HDCG_OK;
 }
 
-int hdcg_set_subspace(hdcg_t h, const int block[4], int nvec, int prec, const void* phi, int on_device,
+int hdcg_set_subspace(hdcg_t h, int level, const int block[4], int nvec, int prec, const void* phi, int on_device,
                       int already_orthonormal) {
   HDCG_ENTRY(h, {
     check_ptr(block, "block");
     check_ptr(phi, "phi");
+    check_level(level);
+    if (level == 2) {
+      HDCG_REQUIRE(c.sub && c.coarse, HDCG_ERR_STATE, "a level-2 subspace needs the level-1 operator");
+      HDCG_REQUIRE(prec == HDCG_F32, HDCG_ERR_ARG, "level-2 vectors are stored in F32");
+      level2_set_subspace(c, *c.coarse, *c.sub, block, nvec, phi, on_device, already_orthonormal);
+      return HDCG_OK;
+    }
     if (!c.sub) c.sub = new Subspace();
     subspace_init(c, *c.sub, block, nvec, prec);
     const size_t bytes = (size_t)nvec * canon_field_bytes(c, HDCG_F64);
@@ -216,9 +234,15 @@ int hdcg_set_subspace(hdcg_t h, const int block[4], int nvec, int prec, const vo
   return HDCG_OK;
 }
 
-int hdcg_get_subspace(hdcg_t h, void* phi_host) {
+int hdcg_get_subspace(hdcg_t h, int level, void* phi_host) {
   HDCG_ENTRY(h, {
     check_ptr(phi_host, "phi");
+    check_level(level);
+    if (level == 2) {
+      HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no level-2 subspace");
+      level2_get_subspace(c, *c.coarse, phi_host);
+      return HDCG_OK;
+    }
     HDCG_REQUIRE(c.sub, HDCG_ERR_STATE, "no subspace");
     const size_t bytes = (size_t)c.sub->nvec * canon_field_bytes(c, HDCG_F64);
     DevMem tmp;
@@ -230,8 +254,16 @@ int hdcg_get_subspace(hdcg_t h, void* phi_host) {
   return HDCG_OK;
 }
 
-int hdcg_build_coarse(hdcg_t h, int prec) {
-  HDCG_ENTRY(h, { build_coarse(c, prec); });
+int hdcg_build_coarse(hdcg_t h, int level, int prec) {
+  HDCG_ENTRY(h, {
+    check_level(level);
+    if (level == 1) {
+      build_coarse(c, prec);
+    } else {
+      HDCG_REQUIRE(c.coarse && c.coarse->l2, HDCG_ERR_STATE, "no level-2 subspace");
+      level2_assemble(c, *c.coarse, prec);
+    }
+  });
   return HDCG_OK;
 }
 
@@ -245,11 +277,33 @@ int hdcg_set_coarse(hdcg_t h, const void* A, int prec, int on_device) {
   return HDCG_OK;
 }
 
-int hdcg_get_coarse(hdcg_t h, void* A_host) {
+int hdcg_get_coarse(hdcg_t h, int level, void* A_host) {
   HDCG_ENTRY(h, {
     check_ptr(A_host, "A");
+    check_level(level);
     HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
-    coarse_export(c, *c.coarse, A_host);
+    if (level == 1) coarse_export(c, *c.coarse, A_host);
+    else level2_export(c, *c.coarse, A_host);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_restrict_coarse(hdcg_t h, const void* x, void* c2, int nrhs) {
+  HDCG_ENTRY(h, {
+    check_ptr(x, "x");
+    check_ptr(c2, "c2");
+    HDCG_REQUIRE(c.coarse && c.coarse->l2, HDCG_ERR_STATE, "no level-2 subspace");
+    level2_restrict_canon(c, *c.coarse, nrhs, x, c2);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_prolong_coarse(hdcg_t h, const void* c2, void* x, int nrhs) {
+  HDCG_ENTRY(h, {
+    check_ptr(x, "x");
+    check_ptr(c2, "c2");
+    HDCG_REQUIRE(c.coarse && c.coarse->l2, HDCG_ERR_STATE, "no level-2 subspace");
+    level2_prolong_canon(c, *c.coarse, nrhs, c2, x);
   });
   return HDCG_OK;
 }
@@ -431,19 +485,22 @@ int hdcg_set_profiling(hdcg_t h, int on) {
         c.prof.launches[i] = 0;
         c.prof.ms[i] = 0;
         c.prof.bytes[i] = 0;
+        c.prof.op_bytes[i] = 0;
       }
     }
   });
   return HDCG_OK;
 }
 
-int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes) {
+int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_ms, double* bytes,
+                         double* op_bytes) {
   HDCG_ENTRY(h, {
     check_op_prec(prec);
     resolve_profile(c);
     if (launches) *launches = c.prof.launches[prec];
     if (total_ms) *total_ms = c.prof.ms[prec];
     if (bytes) *bytes = c.prof.bytes[prec];
+    if (op_bytes) *op_bytes = c.prof.op_bytes[prec];
   });
   return HDCG_OK;
 }

@@ -16,7 +16,6 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
-#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -597,6 +596,17 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   A.defl.lam_h.clear();
   A.graph_cg.reset();
   A.graph_ad1.reset();
+  A.Aacc.release();
+  // a level-2 subspace of the same geometry is kept (subspace reuse); its
+  // operator belongs to the old A and is rebuilt with hdcg_build_coarse(level 2)
+  if (A.l2 && (A.l2->Vc1 != s.Vc || A.l2->n1 != s.nvec)) {
+    delete A.l2;
+    A.l2 = nullptr;
+  }
+  if (A.l2) {
+    A.l2->have_A2 = false;
+    A.l2->graph.reset();
+  }
   A.nvec = s.nvec;
   A.Vc = s.Vc;
   std::vector<int> nb(s.Vc * 81);
@@ -813,9 +823,14 @@ void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec) {
   else if (A.prec == HDCG_F32)
     k_fourier_solve<float2><<<gA, 256, 0, c.stream>>>(F.as<double2>(), dMinv.as<double2>(), dlq.as<int>(), nS, n, s.Vc,
                                                       A.A.as<float2>());
-  else
+  else {
     k_fourier_solve<__half2><<<gA, 256, 0, c.stream>>>(F.as<double2>(), dMinv.as<double2>(), dlq.as<int>(), nS, n, s.Vc,
                                                        A.A.as<__half2>());
+    A.Aacc.ensure(tot * sizeof(float2));
+    k_fourier_solve<float2><<<gA, 256, 0, c.stream>>>(F.as<double2>(), dMinv.as<double2>(), dlq.as<int>(), nS, n, s.Vc,
+                                                      A.Aacc.as<float2>());
+    ++c.launches;
+  }
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
@@ -1201,6 +1216,7 @@ bool coarse_use_tc_single(Ctx& c, Coarse& A) {
 }
 
 int coarse_cg(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol, int maxiter) {
+  if (level2_active(A)) return level1_solve(c, A, 1, rhs, sol, tol, maxiter);
   if (A.defl.nd > 0) {
     if (coarse_tc_supported(A) && A.tc_choice < 0) tune_single(c, A, rhs, sol);
     return coarse_adef1(c, A, 1, rhs, sol, tol, maxiter);
@@ -1279,7 +1295,12 @@ void coarse_import(Ctx& c, Coarse& A, const void* src, int on_device) {
   const unsigned g = (unsigned)((tot + 255) / 256);
   if (A.prec == HDCG_F64) k_coarse_import<double2><<<g, 256, 0, c.stream>>>(in, A.A.as<double2>(), A.nvec, A.Vc);
   else if (A.prec == HDCG_F32) k_coarse_import<float2><<<g, 256, 0, c.stream>>>(in, A.A.as<float2>(), A.nvec, A.Vc);
-  else k_coarse_import<__half2><<<g, 256, 0, c.stream>>>(in, A.A.as<__half2>(), A.nvec, A.Vc);
+  else {
+    k_coarse_import<__half2><<<g, 256, 0, c.stream>>>(in, A.A.as<__half2>(), A.nvec, A.Vc);
+    A.Aacc.ensure(tot * sizeof(float2));
+    k_coarse_import<float2><<<g, 256, 0, c.stream>>>(in, A.Aacc.as<float2>(), A.nvec, A.Vc);
+    ++c.launches;
+  }
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
   A.tc_ready = false;
@@ -1313,24 +1334,24 @@ void coarse_export(Ctx& c, const Coarse& A, void* host) {
 // overlap on the GPU (other streams, other host threads) race on it.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256] = {};
 
-// Device address of the array on the current device: looked up once per
-// device with that device current (the first call on a device does this set-up).
-static char* noalloc_scratch() {
+// Device address of the array on the current device.  The handle looks it up
+// with that device current on its first no-alloc call (and again if the
+// current device changes) and keeps it for its own lifetime: a handle never
+// outlives the CUDA context it was created in, so the address cannot go stale
+// the way a process-wide cache could after a device reset.
+static char* noalloc_scratch(Ctx& c) {
   int dev = 0;
   HDCG_CUDA(cudaGetDevice(&dev));
-  HDCG_REQUIRE(dev >= 0 && dev < 256, HDCG_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (c.noalloc_addr == nullptr || c.noalloc_dev != dev) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
       throw Error{HDCG_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") + cudaGetErrorString(e)};
-    g_noalloc_addr[dev] = p;
+    c.noalloc_addr = p;
+    c.noalloc_dev = dev;
   }
-  return reinterpret_cast<char*>(g_noalloc_addr[dev]);
+  return reinterpret_cast<char*>(c.noalloc_addr);
 }
 
 size_t coarse_apply_noalloc_bytes(const Coarse& A) {
@@ -1344,7 +1365,7 @@ template <typename AT, typename R>
 static void coarse_apply_noalloc_t(Ctx& c, const Coarse& A, const void* x64, void* y64) {
   using V = typename CV<R>::T;
   const size_t nc = A.Vc * A.nvec;
-  char* arena = noalloc_scratch();
+  char* arena = noalloc_scratch(c);
   const unsigned gv = (unsigned)((nc + 255) / 256);
   const V* x;
   V* y;
@@ -1404,22 +1425,29 @@ void restrict_multi(Ctx& c, const Subspace& s, const uint4* v, int vprec, int R,
   cvec_convert(c, G.p, HDCG_F64, cvec, cprec, nc);
 }
 
-// out_r = add_r + sum_k c[b][k][r] phi_k  (tile of all vectors in shared memory)
-template <typename Sp, typename So, typename Rt>
+// out_r = f_r (add_r + sum_k c[b][k][r] phi_k)  (tile of all vectors in shared memory);
+// the added field may be stored in a narrower precision Sa than the output
+template <typename Sp, typename So, typename Rt, typename Sa>
 __global__ void __launch_bounds__(256) k_prolong_multi(const uint4* phi, size_t pstride, int n, BlockArgs ba,
                                                        const typename CV<Rt>::T* __restrict__ cv, int R,
-                                                       uint4* out, const uint4* add, size_t ostride) {
+                                                       uint4* out, const uint4* add, size_t ostride, size_t astride,
+                                                       const double* un_num, const double* un_den) {
   using Ro = typename Store<So>::real;
-  constexpr int C = Store<So>::chunks, P = Store<So>::per_chunk;
+  using Ra = typename Store<Sa>::real;
+  constexpr int C = Store<So>::chunks, P = Store<So>::per_chunk, PA = Store<Sa>::per_chunk;
+  static_assert(PA >= P, "the added field's chunks hold at least one output chunk");
   extern __shared__ __align__(16) unsigned char smraw[];
   Rt* xs = reinterpret_cast<Rt*>(smraw);
   Rt* cs = xs + (size_t)n * TROW;    // [k][r] complex
+  __shared__ Rt unscale[RMAX];
   const size_t b = blockIdx.x;
   for (int q = threadIdx.x; q < n * R; q += blockDim.x) {
     const typename CV<Rt>::T v = cv[b * n * R + q];
     cs[2 * q] = v.x;
     cs[2 * q + 1] = v.y;
   }
+  if (threadIdx.x < RMAX)
+    unscale[threadIdx.x] = (un_num && (int)threadIdx.x < R) ? (Rt)sqrt(un_den[threadIdx.x] / un_num[0]) : Rt(1);
   const int nsites = ba.spb * ba.Ls;
   const int units = R * TILE * C;
   for (int tile0 = 0; tile0 < nsites; tile0 += TILE) {
@@ -1444,34 +1472,55 @@ __global__ void __launch_bounds__(256) k_prolong_multi(const uint4* phi, size_t 
       }
       const size_t site5 = block_site5(ba, b, tile0 + t);
       if (add) {
-        Ro av[P];
-        unpack(So{}, __ldg(add + r * ostride + ch * ba.n5 + site5), av);
+        // the P reals of this output chunk sit in chunk (ch P) / PA of the added field
+        Ra av[PA];
+        unpack(Sa{}, __ldg(add + r * astride + ((ch * P) / PA) * ba.n5 + site5), av);
+        const int off = (ch * P) % PA;
 #pragma unroll
-        for (int i = 0; i < P; ++i) o[i] += (Rt)av[i];
+        for (int i = 0; i < P; ++i) o[i] += (Rt)av[off + i];
       }
+      const Rt f = unscale[r];
       Ro w[P];
 #pragma unroll
-      for (int i = 0; i < P; ++i) w[i] = (Ro)o[i];
+      for (int i = 0; i < P; ++i) w[i] = (Ro)(f * o[i]);
       out[r * ostride + ch * ba.n5 + site5] = pack(So{}, w);
     }
   }
 }
 
+template <typename Sp, typename So, typename Rt, typename Sa>
+static void launch_prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int R, uint4* out, const uint4* add,
+                                 size_t ostride, size_t astride, const double* un_num, const double* un_den) {
+  const int n = s.nvec;
+  const size_t sm = tile_smem<Rt>(n) + (size_t)n * R * 2 * sizeof(Rt);
+  auto fn = k_prolong_multi<Sp, So, Rt, Sa>;
+  set_smem_limit((const void*)fn, sm);
+  fn<<<(unsigned)s.Vc, 256, sm, c.stream>>>(s.vecs.as<uint4>(), s.vec_bytes(c) / 16, n, block_args(c, s),
+                                             (const typename CV<Rt>::T*)cvec, R, out, add, ostride, astride, un_num,
+                                             un_den);
+}
+
 void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R, uint4* out, int oprec,
-                   const uint4* add) {
+                   const uint4* add, int add_prec, const double* un_num, const double* un_den) {
   HDCG_REQUIRE((cprec == HDCG_F64) == (s.prec == HDCG_F64), HDCG_ERR_ARG,
                "coarse vectors are FP64 exactly when the subspace is FP64");
-  const int n = s.nvec;
-  const size_t pstride = s.vec_bytes(c) / 16, ostride = c.field_bytes(oprec) / 16;
+  HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  if (add_prec < 0 || !add) add_prec = oprec;
+  HDCG_REQUIRE(add_prec == oprec || (add_prec == HDCG_F16 && (oprec == HDCG_F32 || oprec == HDCG_F64)),
+               HDCG_ERR_ARG, "prolongation: the added field is in the output precision or FP16");
+  const size_t ostride = c.field_bytes(oprec) / 16, astride = c.field_bytes(add_prec) / 16;
   DISPATCH_SUB(s.prec, Sp, {
-    DISPATCH_PREC(oprec, So, {
-      using Rt = typename std::conditional<std::is_same<Sp, f64_t>::value, double, float>::type;
-      const size_t sm = tile_smem<Rt>(n) + (size_t)n * R * 2 * sizeof(Rt);
-      auto fn = k_prolong_multi<Sp, So, Rt>;
-      set_smem_limit((const void*)fn, sm);
-      fn<<<(unsigned)s.Vc, 256, sm, c.stream>>>(s.vecs.as<uint4>(), pstride, n, block_args(c, s),
-                                                 (const typename CV<Rt>::T*)cvec, R, out, add, ostride);
-    });
+    using Rt = typename std::conditional<std::is_same<Sp, f64_t>::value, double, float>::type;
+    if (add_prec != oprec) {
+      if (oprec == HDCG_F32)
+        launch_prolong_multi<Sp, f32_t, Rt, f16_t>(c, s, cvec, R, out, add, ostride, astride, un_num, un_den);
+      else
+        launch_prolong_multi<Sp, f64_t, Rt, f16_t>(c, s, cvec, R, out, add, ostride, astride, un_num, un_den);
+    } else {
+      DISPATCH_PREC(oprec, So, {
+        launch_prolong_multi<Sp, So, Rt, So>(c, s, cvec, R, out, add, ostride, astride, un_num, un_den);
+      });
+    }
   });
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
@@ -1751,6 +1800,7 @@ static int coarse_cg_multi_t(Ctx& c, Coarse& A, int R, const void* rhs, void* so
 int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter, double shift,
                     bool deflate) {
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
+  if (deflate && shift == 0.0 && level2_active(A)) return level1_solve(c, A, R, rhs, sol, tol, maxiter);
   if (deflate && A.defl.nd > 0 && shift == 0.0) return coarse_adef1(c, A, R, rhs, sol, tol, maxiter);
   if (coarse_tc_supported(A)) return coarse_cg_tc(c, A, R, rhs, sol, tol, maxiter, shift);
   if (A.prec == HDCG_F64) return coarse_cg_multi_t<double2, double>(c, A, R, rhs, sol, tol, maxiter, shift);

@@ -22,6 +22,30 @@ struct Subspace {
   }
 };
 
+// blocked second coarsening of the little Dirac operator (level2.cu): Sec. 2's
+// construction on the coarse lattice; vectors FP32, A2 FP64, its inverse dense
+struct Level2 {
+  int block[4] = {0, 0, 0, 0};   // level-2 block extents (coarse sites)
+  int cdims[4] = {0, 0, 0, 0};   // level-2 lattice extents
+  size_t Vc2 = 0;                // level-2 sites
+  int nvec = 0;                  // Nvec2
+  int spb = 0;                   // coarse sites per level-2 block
+  size_t Vc1 = 0;                // coarse sites of the operator it was built for
+  int n1 = 0;                    // and its Nvec
+  DevMem phi;                    // [nvec][Vc1 * n1] complex float, block-orthonormal
+  DevMem blk_of_site;            // int32 [Vc1]
+  DevMem sites;                  // int32 [Vc2][spb], ascending
+  DevMem coords;                 // int32 [Vc2][4]
+  DevMem cnbr2;                  // int32 [Vc2][81]
+  DevMem A2;                     // [Vc2][81][j][k] complex double (canonical)
+  DevMem Ainv;                   // dense [N2][N2] inverse of A2, N2 = Vc2 * nvec (inv_prec)
+  int inv_prec = HDCG_F32;
+  bool have_A2 = false;
+  DevMem work, ctl;              // level-1 solver vectors and control block
+  int last_iters = 2;
+  CapturedGraph graph;
+};
+
 struct Coarse {
   int prec = HDCG_F32;      // storage of A (F64, F32 or F16); vectors: F64 if A is F64 else F32
   int nvec = 0;
@@ -47,6 +71,14 @@ struct Coarse {
     std::vector<double> lam_h;   // +inf marks a pair dropped from Q (non-positive or ~0)
     int dropped = 0;
   } defl;
+  // an FP16 operator keeps an FP32 copy (same layout as A) from which the
+  // level-2 operator is contracted
+  DevMem Aacc;
+  Level2* l2 = nullptr;
+  Coarse() = default;
+  Coarse(const Coarse&) = delete;
+  Coarse& operator=(const Coarse&) = delete;
+  ~Coarse() { delete l2; }
   int vec_prec() const { return prec == HDCG_F64 ? HDCG_F64 : HDCG_F32; }
   size_t vec_bytes() const { return Vc * nvec * (vec_prec() == HDCG_F64 ? 16 : 8); }
 };
@@ -81,6 +113,27 @@ int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, dou
 // single right-hand side: time both coarse apply paths once and keep the faster
 bool coarse_use_tc_single(Ctx& c, Coarse& A);
 
+// [R][ne] complex double (canonical) <-> [ne][R] complex float (device, asynchronous)
+void coarse_canon_to_multi(Ctx& c, const void* in64, float2* out, size_t ne, int R);
+void coarse_multi_to_canon(Ctx& c, const float2* in, void* out64, size_t ne, int R);
+
+// blocked second coarsening (level2.cu)
+void level2_init(Ctx& c, Coarse& A, const Subspace& s, const int block[4], int nvec);
+void level2_build_subspace(Ctx& c, Coarse& A, const Subspace& s, const hdcg_subspace_params& p);
+void level2_set_subspace(Ctx& c, Coarse& A, const Subspace& s, const int block[4], int nvec, const void* phi,
+                         int on_device, int already_orthonormal);
+void level2_get_subspace(Ctx& c, const Coarse& A, void* host);
+void level2_orthonormalise(Ctx& c, Level2& L);
+// A2 = P2^dag A P2 and its dense inverse (stored in inv_prec: F32 or F64)
+void level2_assemble(Ctx& c, Coarse& A, int inv_prec);
+void level2_export(Ctx& c, const Coarse& A, void* host);
+// c2 = R2 x, x = P2 c2 on canonical vectors [R][Vc][Nvec] / [R][Vc2][Nvec2] (complex double, device)
+void level2_restrict_canon(Ctx& c, const Coarse& A, int R, const void* x64, void* c64);
+void level2_prolong_canon(Ctx& c, const Coarse& A, int R, const void* c64, void* x64);
+bool level2_active(const Coarse& A);
+// level-1 solve A x = b (FP32 [e][r]) by A-DEF2 with Q2 = P2 A2^-1 R2; returns iterations
+int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+
 // subspace geometry (host tables -> device)
 void subspace_init(Ctx& c, Subspace& s, const int block[4], int nvec, int prec);
 // Gaussian noise in every subspace vector (splitmix64 counter stream, Box-Muller),
@@ -113,8 +166,12 @@ size_t coarse_apply_noalloc_bytes(const Coarse& A);
 void coarse_apply_noalloc(Ctx& c, const Coarse& A, const void* x64, void* y64);
 // several right-hand sides: coarse vectors [a][k][r]
 void restrict_multi(Ctx& c, const Subspace& s, const uint4* v, int vprec, int R, void* cvec, int cprec);
+// out_r = f_r (add_r + P c_r); add (may be null) in oprec or, for an FP32/FP64
+// output, in FP16 (add_prec); f_r = sqrt(un_den[r] / un_num[0]) when un_num is
+// given (undoes convert_scaled's unit-RMS scaling), else 1
 void prolong_multi(Ctx& c, const Subspace& s, const void* cvec, int cprec, int R, uint4* out, int oprec,
-                   const uint4* add);
+                   const uint4* add, int add_prec = -1, const double* un_num = nullptr,
+                   const double* un_den = nullptr);
 // coarse CG on (A + shift) for R right-hand sides; with deflate and a second-level
 // deflation space (and no shift) the solve is A-DEF1 instead
 int coarse_cg_multi(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter,

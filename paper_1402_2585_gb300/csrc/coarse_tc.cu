@@ -1,5 +1,5 @@
 // Little Dirac operator on the tensor cores (tcgen05), for 1..16 right-hand
-// sides at once:  Y_a = sum_{l in {-1,0,1}^4} A^{a,a+l} X_{a+l}  (Sec. 4.3).
+// sides at once:  Y_a = sum_{l in {-1,0,1}^4} A^{a,a+l} X_{a+l}  (Sec. 5.1).
 //
 // The complex Nvec x Nvec block A^{a,l} enters the MMA as a real matrix with
 // interleaved rows m = 2j + ri (ri = 0: Re A_jk, ri = 1: Im A_jk), so
@@ -736,6 +736,17 @@ __global__ void k_multi_to_canon(const V* __restrict__ in, double2* out, size_t 
   const size_t e = t / R;
   const int r = (int)(t % R);
   out[(size_t)r * ne + e] = make_double2((double)in[t].x, (double)in[t].y);
+}
+
+void coarse_canon_to_multi(Ctx& c, const void* in64, float2* out, size_t ne, int R) {
+  k_canon_to_multi<float2><<<(unsigned)((ne * R + 255) / 256), 256, 0, c.stream>>>((const double2*)in64, out, ne, R);
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
+}
+void coarse_multi_to_canon(Ctx& c, const float2* in, void* out64, size_t ne, int R) {
+  k_multi_to_canon<float2><<<(unsigned)((ne * R + 255) / 256), 256, 0, c.stream>>>(in, (double2*)out64, ne, R);
+  HDCG_CUDA(cudaGetLastError());
+  ++c.launches;
 }
 
 int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, double tol, int maxiter) {

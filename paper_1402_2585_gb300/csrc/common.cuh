@@ -184,10 +184,11 @@ __device__ __forceinline__ void warp_sum(double (&v)[NV], int active = RED_RHS) 
       if (red_active<NV>(i, active)) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
 }
 
-template <int NV>
+// PRE: the values are already summed over each warp (valid in lane 0)
+template <int NV, bool PRE = false>
 __device__ void block_sum(double (&v)[NV], int active = RED_RHS) {
   __shared__ double sh[32][NV];
-  warp_sum<NV>(v, active);
+  if (!PRE) warp_sum<NV>(v, active);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
   if (lane == 0)
@@ -213,9 +214,10 @@ struct Reduction {
 };
 
 // Returns true in every thread of the last block (after the totals are stored).
-template <int NV>
+// PRE: v already holds per-warp sums in lane 0 (see block_sum).
+template <int NV, bool PRE = false>
 __device__ bool grid_reduce(double (&v)[NV], const Reduction& red, int active = RED_RHS) {
-  block_sum<NV>(v, active);
+  block_sum<NV, PRE>(v, active);
   __shared__ bool last;
   const unsigned y = blockIdx.y;
   double* partials = red.partials + (size_t)NV * gridDim.x * y;

@@ -88,7 +88,8 @@ struct HopProfile {
   std::vector<int> pending_prec;
   long long launches[NPREC] = {};
   double ms[NPREC] = {};
-  double bytes[NPREC] = {};
+  double bytes[NPREC] = {};      // everything the launches move (fused epilogues included)
+  double op_bytes[NPREC] = {};   // the operator's own bytes only
 };
 
 // solve-phase timing (CUDA events on the stream, resolved on request)
@@ -127,6 +128,8 @@ struct Ctx {
   PhaseProfile phases;
   long long launches = 0;
   std::string err;
+  void* noalloc_addr = nullptr;   // device address of the no-alloc scratch array (coarse.cu)
+  int noalloc_dev = -1;           // device it was looked up on
 
   size_t field_bytes(int prec) const { return n5 * 24 * bytes_per_real(prec); }
   uint4* scratch(int prec, int i, int nfields = 1) {

@@ -273,6 +273,15 @@ void launch_hop(Ctx& c, int pass, int prec, const uint4* in, const uint4* in2, u
   for (int j = 0; j < 6; ++j) a.rpow[j] = c.co.rpow[j];
   a.sD = epi.sD;
   a.lam = epi.lam;
+  a.fb = (float)a.b;
+  a.fc = (float)a.c;
+  a.falpha = (float)a.alpha;
+  a.fbeta = (float)a.beta;
+  a.fmass = (float)a.mass;
+  a.fminv_norm = (float)a.minv_norm;
+  for (int j = 0; j < 6; ++j) a.frpow[j] = (float)a.rpow[j];
+  a.fsD = (float)a.sD;
+  a.flam = (float)a.lam;
   a.cg_x = epi.cg_x;
   a.cg_r = epi.cg_r;
   a.cg_p = epi.cg_p;
@@ -310,6 +319,7 @@ void launch_hop(Ctx& c, int pass, int prec, const uint4* in, const uint4* in2, u
     c.prof.pending.push_back(ev0);
     c.prof.pending.push_back(ev1);
     c.prof.pending_prec.push_back(prec);
+    c.prof.op_bytes[prec] += epi.nrhs * hop_bytes(c, pass, prec, false);
     c.prof.bytes[prec] += epi.nrhs * (hop_bytes(c, pass, prec, epi.extra != nullptr) +
                                       (epi.cg_r ? (double)c.n5 * 24 * bytes_per_real(prec) * (epi.extra ? 4.0 : 5.0)
                                                 : 0.0));

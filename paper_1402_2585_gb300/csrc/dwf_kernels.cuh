@@ -22,6 +22,9 @@ struct HopArgs {
   int Ls, lslog2;
   double b, c, alpha, beta, mass, minv_norm, rpow[6];
   double sD, lam;
+  // the same coefficients rounded to float on the host: the FP32/16-bit passes
+  // read these, so no thread converts from double (GB300's FP64 pipe is narrow)
+  float fb, fc, falpha, fbeta, fmass, fminv_norm, frpow[6], fsD, flam;
   Reduction red;
   int do_red;
   // fused CG step in pass D (cg_r != null): w = out is not stored; instead
@@ -39,6 +42,11 @@ struct HopArgs {
   size_t fstride;
   const int* al_mask;
 };
+
+// coefficient in the arithmetic type R: the host-rounded float for FP32
+// arithmetic, the double otherwise (FP64 and double-float passes)
+template <typename R> __device__ __forceinline__ R sc(double d, float) { return R(d); }
+template <> __device__ __forceinline__ float sc<float>(double, float f) { return f; }
 
 // ------------------------------------------------------------------------------
 // link loads: 9 complex of one link into 18 reals.  Links are stored padded to
@@ -138,21 +146,21 @@ __device__ __forceinline__ void apply_lin(R* v, R a, R b, int s, int Ls, R m) {
 // v <- M_ee^-1 v (DAG: M_ee^-dag) by doubling: A_{j+1} = A_j + r^{2^j} P^{2^j} A_j
 template <typename R, bool DAG>
 __device__ __forceinline__ void apply_minv(R* v, int s, const HopArgs& a) {
-  const R m = (R)a.mass;
+  const R m = sc<R>(a.mass, a.fmass);
   const int Ls = a.Ls;
   for (int j = 0; j < a.lslog2; ++j) {
     const int d = 1 << j;
     const int up_src = (s + d) & (Ls - 1), dn_src = (s - d) & (Ls - 1);
     const R up_f = (s + d >= Ls) ? -m : R(1), dn_f = (s < d) ? -m : R(1);
     const int sp = DAG ? up_src : dn_src, sm = DAG ? dn_src : up_src;
-    const R rp = (R)a.rpow[j];
+    const R rp = sc<R>(a.rpow[j], a.frpow[j]);
     const R cp = rp * (DAG ? up_f : dn_f), cm = rp * (DAG ? dn_f : up_f);
 #pragma unroll
     for (int i = 0; i < 12; ++i) v[i] += cp * shfl_any(v[i], sp, Ls);
 #pragma unroll
     for (int i = 12; i < 24; ++i) v[i] += cm * shfl_any(v[i], sm, Ls);
   }
-  const R nrm = (R)a.minv_norm;
+  const R nrm = sc<R>(a.minv_norm, a.fminv_norm);
 #pragma unroll
   for (int i = 0; i < 24; ++i) v[i] *= nrm;
 }
@@ -255,7 +263,7 @@ __device__ __forceinline__ void hop_pair(const HopArgs& a, const uint4* in, cons
     for (int side = 0; side < 2; ++side) {
       R ps[24];
       load_spinor<St, R>(in, (size_t)nbv[MU + 4 * side] * a.Ls + s, a.n5, ps);
-      if (KIN) apply_lin<R, false>(ps, (R)a.b, (R)a.c, s, a.Ls, (R)a.mass);
+      if (KIN) apply_lin<R, false>(ps, sc<R>(a.b, a.fb), sc<R>(a.c, a.fc), s, a.Ls, sc<R>(a.mass, a.fmass));
       R h[12], uh[12], U[18];
       load_link((const LT*)nullptr, lk + (MU + 4 * side) * LG, U);
       if (side == 0) {
@@ -273,9 +281,9 @@ __device__ __forceinline__ void hop_pair(const HopArgs& a, const uint4* in, cons
     load_spinor<St, R>(in, (size_t)nbv[MU] * a.Ls + s, a.n5, pf);
     load_spinor<St, R>(in, (size_t)nbv[MU + 4] * a.Ls + s, a.n5, pb);
     if (KIN) {
-      const R m = (R)a.mass;
-      apply_lin<R, false>(pf, (R)a.b, (R)a.c, s, a.Ls, m);
-      apply_lin<R, false>(pb, (R)a.b, (R)a.c, s, a.Ls, m);
+      const R m = sc<R>(a.mass, a.fmass), kb = sc<R>(a.b, a.fb), kc = sc<R>(a.c, a.fc);
+      apply_lin<R, false>(pf, kb, kc, s, a.Ls, m);
+      apply_lin<R, false>(pb, kb, kc, s, a.Ls, m);
     }
     R h[12], uh[12], U[18];
     project<MU, SF>(pf, h);
@@ -303,7 +311,7 @@ __device__ __forceinline__ void hop_raw(const HopArgs& a, const uint4 (&raw)[8][
 #pragma unroll
       for (int i = 0; i < 8; ++i) ps[c * 8 + i] = (R)t[i];
     }
-    if (KIN) apply_lin<R, false>(ps, (R)a.b, (R)a.c, s, a.Ls, (R)a.mass);
+    if (KIN) apply_lin<R, false>(ps, sc<R>(a.b, a.fb), sc<R>(a.c, a.fc), s, a.Ls, sc<R>(a.mass, a.fmass));
     R h[12], uh[12], U[18];
     load_link((const LT*)nullptr, lk + (MU + 4 * side) * LG, U);
     if (side == 0) {
@@ -315,6 +323,42 @@ __device__ __forceinline__ void hop_raw(const HopArgs& a, const uint4 (&raw)[8][
       su3_mul<R>(U, h, uh);
       reconstruct_add<MU, -SF>(uh, acc);
     }
+  }
+}
+
+// |acc|^2 of the pass into the FP64 grid reduction.  FP32 arithmetic: each
+// warp sums its lanes' float partials by double-float TwoSum steps on the FP32
+// pipes (about 48 bits) and only the per-warp totals are added in FP64; the
+// FP64 and double-float passes reduce in FP64 throughout.
+template <typename R>
+__device__ __forceinline__ void hop_norm2(const R* acc, bool active, const Reduction& red) {
+  if constexpr (std::is_same<R, float>::value) {
+    float t = 0.f;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < 24; ++i) t = fmaf(acc[i], acc[i], t);
+    }
+    float hi = t, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(FULL_MASK, hi, o), ol = __shfl_xor_sync(FULL_MASK, lo, o);
+      float sh, eh;
+      two_sum(hi, oh, sh, eh);
+      eh = __fadd_rn(eh, __fadd_rn(lo, ol));
+      fast_two_sum(sh, eh, hi, lo);
+    }
+    double v[1] = {(double)hi + (double)lo};
+    grid_reduce<1, true>(v, red);
+  } else {
+    double nrm2 = 0.0;
+    if (active) {
+      R t = 0;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) t += acc[i] * acc[i];
+      nrm2 = (double)t;
+    }
+    double v[1] = {nrm2};
+    grid_reduce<1>(v, red);
   }
 }
 
@@ -347,7 +391,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   const int s = threadIdx.x & (a.Ls - 1);
   const size_t x4 = active ? (gtid >> a.lslog2) : 0;
   const size_t site5 = x4 * a.Ls + s;
-  const R m = (R)a.mass;
+  const R m = sc<R>(a.mass, a.fmass);
+  const R kb = sc<R>(a.b, a.fb), kc = sc<R>(a.c, a.fc);
 
   R acc[24];
 #pragma unroll
@@ -378,57 +423,64 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
     hop_pair<St, R, LT, 3, SF, PASS == PASS_A && MOB>(a, in, nbv, lk, s, acc);
   }
 
-  double nrm2 = 0.0;
   if (PASS == PASS_A) {
     apply_minv<R, false>(acc, s, a);
     if (MOB) {
-      apply_lin<R, false>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+      apply_lin<R, false>(acc, kb, kc, s, a.Ls, m);
     } else {
-      const R bb = (R)(a.b * a.b);
+      const R bb = kb * kb;
 #pragma unroll
       for (int i = 0; i < 24; ++i) acc[i] *= bb;
     }
   } else if (PASS == PASS_C) {
     if (MOB) {
-      apply_lin<R, true>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+      apply_lin<R, true>(acc, kb, kc, s, a.Ls, m);
     } else {
 #pragma unroll
-      for (int i = 0; i < 24; ++i) acc[i] *= (R)a.b;
+      for (int i = 0; i < 24; ++i) acc[i] *= kb;
     }
     apply_minv<R, true>(acc, s, a);
   } else {
     // B, D: out = M_oo^(dag) in2 - K^(dag) acc / 4   (B has no K on this side)
     if (PASS == PASS_D) {
       if (MOB) {
-        apply_lin<R, true>(acc, (R)a.b, (R)a.c, s, a.Ls, m);
+        apply_lin<R, true>(acc, kb, kc, s, a.Ls, m);
       } else {
 #pragma unroll
-        for (int i = 0; i < 24; ++i) acc[i] *= (R)a.b;
+        for (int i = 0; i < 24; ++i) acc[i] *= kb;
       }
     }
     R self[24];
     load_spinor<St, R>(a.in2 + roff, site5, a.n5, self);
-    apply_lin<R, DAG>(self, (R)a.alpha, (R)a.beta, s, a.Ls, m);
+    apply_lin<R, DAG>(self, sc<R>(a.alpha, a.falpha), sc<R>(a.beta, a.fbeta), s, a.Ls, m);
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = self[i] - R(0.25) * acc[i];
     if (PASS == PASS_D) {
-      const R sD = (R)a.sD;
+      const R sD = sc<R>(a.sD, a.fsD);
 #pragma unroll
       for (int i = 0; i < 24; ++i) acc[i] *= sD;
       if (a.extra) {
         R ex[24];
         load_spinor<St, R>(a.extra + roff, site5, a.n5, ex);
-        const R lam = (R)a.lam;
+        const R lam = sc<R>(a.lam, a.flam);
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] += lam * ex[i];
       }
     }
   }
   if (PASS == PASS_D && a.cg_r) {
-    double den = a.al_den0[rhs];
-    if (a.al_den1) den += a.al_lam * a.al_den1[rhs];
-    const bool live = a.al_mask == nullptr || a.al_mask[rhs] != 0;
-    const R alpha = (R)((den != 0.0 && live) ? a.al_num[rhs] / den : 0.0);
+    // alpha of the fused CG step: one FP64 division per CTA, shared
+    __shared__ double s_alpha;
+    __shared__ float s_alphaf;
+    if (threadIdx.x == 0) {
+      double den = a.al_den0[rhs];
+      if (a.al_den1) den += a.al_lam * a.al_den1[rhs];
+      const bool live = a.al_mask == nullptr || a.al_mask[rhs] != 0;
+      s_alpha = (den != 0.0 && live) ? a.al_num[rhs] / den : 0.0;
+      s_alphaf = (float)s_alpha;
+    }
+    __syncthreads();
+    const R alpha = sc<R>(s_alpha, s_alphaf);
     if (active) {
       R rv[24], xv[24], pv[24];
       load_spinor<St, R>(a.cg_r + roff, site5, a.n5, rv);
@@ -446,16 +498,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   } else if (active) {
     store_spinor<St, R>(a.out + roff, site5, a.n5, acc);
   }
-  if (a.do_red) {
-    if (active) {
-      R t = 0;
-#pragma unroll
-      for (int i = 0; i < 24; ++i) t += acc[i] * acc[i];
-      nrm2 = (double)t;
-    }
-    double v[1] = {nrm2};
-    grid_reduce<1>(v, a.red);
-  }
+  if (a.do_red) hop_norm2<R>(acc, active, a.red);
 }
 
 

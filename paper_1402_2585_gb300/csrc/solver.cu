@@ -34,7 +34,8 @@ enum {
 // device scalar slots (doubles)
 enum {
   D_PW = 0, D_RR = 1, D_RY = 2, D_RYN = 3 /* 2 */, D_BB = 6, D_TMP = 7, D_NREAL = 8,
-  D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27
+  D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27,
+  D_RYO = 30 /* 2 */
 };
 
 static double* dsc(Ctx& c, int slot) { return c.scalars.as<double>() + slot * RMAX; }
@@ -204,25 +205,25 @@ static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdc
   }
 }
 
-// r64 = b - H64 x_hi; returns |r64|^2 (host), r (op) = r64
-// r64 = b64 - H x64 for R right-hand sides with the double-float operator (FP64
-// accuracy on the FP32 units): x and b enter as double-float copies, r leaves as FP64
-static void residual_df(Ctx& c, int R, const uint4* b64, const uint4* x64, uint4* r64) {
-  uint4* xd = c.scratch(HDCG_DF64, 5, R);
-  uint4* bd = c.scratch(HDCG_DF64, 6, R);
-  uint4* rd = c.scratch(HDCG_DF64, 7, R);
-  convert_field(c, x64, HDCG_F64, xd, HDCG_DF64, R);
-  convert_field(c, b64, HDCG_F64, bd, HDCG_DF64, R);
-  if (R == 1) apply_mdagm(c, HDCG_DF64, xd, rd, nullptr, -1.0, 1.0, bd);
-  else apply_mdagm_multi(c, HDCG_DF64, R, xd, rd, nullptr, -1.0, 1.0, bd);
-  convert_field(c, rd, HDCG_DF64, r64, HDCG_F64, R);
+// r64 = b64 - H x64 for one right-hand side with the double-float operator (FP64
+// accuracy on the FP32 units): x and b enter as double-float copies, r leaves as
+// FP64.  Several right-hand sides run one after another, so the double-float
+// work fields are one field each whatever the batch.
+static void residual_df(Ctx& c, const uint4* b64, const uint4* x64, uint4* r64) {
+  uint4* xd = c.scratch(HDCG_DF64, 5);
+  uint4* bd = c.scratch(HDCG_DF64, 6);
+  uint4* rd = c.scratch(HDCG_DF64, 7);
+  convert_field(c, x64, HDCG_F64, xd, HDCG_DF64);
+  convert_field(c, b64, HDCG_F64, bd, HDCG_DF64);
+  apply_mdagm(c, HDCG_DF64, xd, rd, nullptr, -1.0, 1.0, bd);
+  convert_field(c, rd, HDCG_DF64, r64, HDCG_F64);
 }
 
 static double true_residual(Ctx& c, int op, const uint4* b64, const uint4* xhi, uint4* r, hdcg_stats* st) {
   uint4* r64 = c.scratch(HDCG_F64, SL_R64);
   {
     PhaseTimer pt(c, PH_H_F64);
-    residual_df(c, 1, b64, xhi, r64);
+    residual_df(c, b64, xhi, r64);
   }
   if (st) ++st->n_mdagm_f64;
   norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR));
@@ -338,7 +339,8 @@ static int solve_one(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdc
 // subspace and the little Dirac operator once per step for all of them.
 // ---------------------------------------------------------------------------
 static void apply_Q_multi(Ctx& c, int sp, int R, const uint4* t, uint4* out, int oprec, const uint4* add,
-                          const hdcg_params& prm, hdcg_stats* st) {
+                          const hdcg_params& prm, hdcg_stats* st, int add_prec = -1,
+                          const double* un_num = nullptr, const double* un_den = nullptr) {
   Subspace& s = *c.sub;
   Coarse& A = *c.coarse;
   const int cp = A.vec_prec();
@@ -361,9 +363,13 @@ static void apply_Q_multi(Ctx& c, int sp, int R, const uint4* t, uint4* out, int
     if (it > st->coarse_iterations_max) st->coarse_iterations_max = it;
   }
   PhaseTimer pt(c, PH_TRANSFER);
-  prolong_multi(c, s, cout, cp, R, out, oprec, add);
+  prolong_multi(c, s, cout, cp, R, out, oprec, add, add_prec, un_num, un_den);
 }
 
+// y = M1 r for R right-hand sides.  Work fields: rs, z and the CG's residual and
+// direction (sloppy precision); r - H z reuses the CG direction's slot.  A
+// 16-bit preconditioner's output is prolonged straight into y in the outer
+// precision, with z added from FP16 and the unit-RMS scaling undone there.
 static void apply_M1_multi(Ctx& c, int op, int sp, int R, const uint4* r, uint4* y, const hdcg_params& prm,
                            hdcg_stats* st) {
   const uint4* rs = r;
@@ -379,17 +385,22 @@ static void apply_M1_multi(Ctx& c, int op, int sp, int R, const uint4* r, uint4*
     rs = t;
   }
   uint4* z = c.scratch(sp, SL_Z, R);
-  uint4* t = c.scratch(sp, SL_T, R);
   int nm = 0;
+  uint4* t;
   {
     PhaseTimer pt(c, PH_H_SLOPPY);
     cg_shifted(c, sp, rs, z, prm.mirs_shift, prm.mirs_iter, 0.0, prm.mirs_iter, &nm, R);
+    t = c.scratch(sp, SL_MP, R);   // the CG's direction is dead now
     apply_mdagm_multi(c, sp, R, z, t, nullptr, -1.0, 1.0, rs);  // t = r - H z
     nm += R;
   }
   if (st) st->n_mdagm_sloppy += nm;
   if (sp == op) {
     apply_Q_multi(c, sp, R, t, y, sp, z, prm, st);
+  } else if (scaled && sp == HDCG_F16) {
+    // the coarse-grid correction amplifies low modes by up to 1 / lambda_min(H),
+    // beyond the FP16 range: y = unscale(z + Q t) is formed in the outer precision
+    apply_Q_multi(c, sp, R, t, y, op, z, prm, st, HDCG_F16, dsc(c, D_NREAL), dsc(c, D_TMP));
   } else if (scaled) {
     uint4* zf = c.scratch(HDCG_F32, SL_Z, R);
     uint4* yf = c.scratch(HDCG_F32, SL_MRES, R);
@@ -410,9 +421,8 @@ static void start_vector_multi(Ctx& c, int sp, int R, const uint4* b64, uint4* x
   if (scaled) {
     norm2(c, b64, HDCG_F64, 0, dsc(c, D_TMP), R);
     convert_scaled(c, b64, HDCG_F64, bs, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0, R);
-    uint4* x0 = c.scratch(HDCG_F32, SL_T, R);
-    apply_Q_multi(c, sp, R, bs, x0, HDCG_F32, nullptr, prm, st);
-    convert_scaled(c, x0, HDCG_F32, xhi, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), 1, R);
+    // x_hi = unscale(Q b_s), prolonged straight into FP64
+    apply_Q_multi(c, sp, R, bs, xhi, HDCG_F64, nullptr, prm, st, -1, dsc(c, D_NREAL), dsc(c, D_TMP));
   } else {
     convert_field(c, b64, HDCG_F64, bs, sp, R);
     uint4* x0 = c.scratch(sp, SL_T, R);
@@ -421,18 +431,22 @@ static void start_vector_multi(Ctx& c, int sp, int R, const uint4* b64, uint4* x
   }
 }
 
-// r64_k = b_k - H64 x_k for all right-hand sides; rr[k] on the host; r (op) = r64
+// r64_k = b_k - H64 x_k for all right-hand sides, one at a time; rr[k] on the
+// host; r_k (op) = r64_k
 static void true_residual_multi(Ctx& c, int op, int R, const uint4* b64, const uint4* xhi, uint4* r, double* rr,
                                 hdcg_stats* st) {
-  uint4* r64 = c.scratch(HDCG_F64, SL_R64, R);
-  {
-    PhaseTimer pt(c, PH_H_F64);
-    residual_df(c, R, b64, xhi, r64);
+  uint4* r64 = c.scratch(HDCG_F64, SL_R64);
+  const size_t f64 = c.field_bytes(HDCG_F64) / 16, fop = c.field_bytes(op) / 16;
+  for (int k = 0; k < R; ++k) {
+    {
+      PhaseTimer pt(c, PH_H_F64);
+      residual_df(c, b64 + k * f64, xhi + k * f64, r64);
+    }
+    norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR) + k);
+    if (op != HDCG_F64) convert_field(c, r64, HDCG_F64, r + k * fop, op);
+    else copy_field(c, HDCG_F64, r64, r + k * fop);
   }
   if (st) st->n_mdagm_f64 += R;
-  norm2(c, r64, HDCG_F64, 0, dsc(c, D_RR), R);
-  if (op != HDCG_F64) convert_field(c, r64, HDCG_F64, r, op, R);
-  else copy_fields(c, HDCG_F64, r64, r, R);
   HDCG_CUDA(cudaMemcpyAsync(rr, dsc(c, D_RR), R * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
@@ -448,7 +462,6 @@ static int solve_batch(Ctx& c, const uint4* b64, uint4* x64, int R, double tol, 
   uint4* r = c.scratch(op, SL_R, R);
   uint4* p = c.scratch(op, SL_P, R);
   uint4* y = c.scratch(op, SL_Y, R);
-  uint4* yn = c.scratch(op, SL_YN, R);
   uint4* xhi = x64;
   DevMem dmask;
   dmask.ensure(RMAX * sizeof(int));
@@ -523,17 +536,18 @@ static int solve_batch(Ctx& c, const uint4* b64, uint4* x64, int R, double tol, 
       }
     }
     if (adef2) {
-      apply_M1_multi(c, op, sp, R, r, yn, prm, st);
-      redot2(c, op, r, yn, y, dsc(c, D_RYN), R);
+      // (r, y_old) for the flexible beta, then y_new overwrites y_old
+      if (prm.flexible) redot2(c, op, r, y, nullptr, dsc(c, D_RYO), R);
+      apply_M1_multi(c, op, sp, R, r, y, prm, st);
+      redot2(c, op, r, y, nullptr, dsc(c, D_RYN), R);
       ScalarRef be;
       be.num = dsc(c, D_RYN);
       be.den0 = dsc(c, D_RY);
-      be.den1 = prm.flexible ? dsc(c, D_RYN) + 1 : nullptr;
+      be.den1 = prm.flexible ? dsc(c, D_RYO) : nullptr;
       be.stride = 2;
-      update_p(c, op, p, yn, be, nullptr, R);
+      update_p(c, op, p, y, be, nullptr, R);
       HDCG_CUDA(cudaMemcpy2DAsync(dsc(c, D_RY), sizeof(double), dsc(c, D_RYN), 2 * sizeof(double), sizeof(double), R,
                                   cudaMemcpyDeviceToDevice, c.stream));
-      std::swap(y, yn);
     } else {
       ScalarRef be;
       be.num = dsc(c, D_RR);
@@ -550,6 +564,34 @@ static int solve_batch(Ctx& c, const uint4* b64, uint4* x64, int R, double tol, 
   return status;
 }
 
+// Device bytes one more right-hand side of a batch needs: FP64 b and x, the
+// outer recursion (x_lo, r, p, y and the two intermediate fields of H), the
+// preconditioner's fields (r_s, z, the CG's residual and direction, and the
+// intermediates of the sloppy H), and host staging of b and x.
+static size_t bytes_per_rhs(const Ctx& c, const hdcg_params& prm, bool on_device) {
+  const int op = prm.outer_prec, sp = prm.sloppy_prec;
+  size_t n = 2 * c.field_bytes(HDCG_F64) + 6 * c.field_bytes(op);
+  if (prm.algorithm == HDCG_ALG_ADEF2) n += 4 * c.field_bytes(sp) + (sp != op ? 2 * c.field_bytes(sp) : 0);
+  if (!on_device) n += 2 * c.n5 * 12 * sizeof(double2);
+  return n;
+}
+
+// Right-hand sides per batch: at most 16, and no more than the device memory
+// free now (plus what this handle's work fields already hold, which a batch
+// reuses) can take, keeping 4 GiB for the library's other buffers.
+static int batch_size(Ctx& c, const hdcg_params& prm, int nrhs, bool on_device) {
+  if (!prm.batch) return 1;
+  size_t freeb = 0, total = 0;
+  HDCG_CUDA(cudaMemGetInfo(&freeb, &total));
+  size_t held = c.canon_in.bytes + c.canon_out.bytes;
+  for (int p = 0; p < NPREC; ++p)
+    for (int i = 0; i < 20; ++i) held += c.scratch_f[p][i].bytes;
+  const size_t avail = freeb + held, reserve = size_t(4) << 30;
+  const size_t per = bytes_per_rhs(c, prm, on_device);
+  const size_t fit = avail > reserve ? (avail - reserve) / per : 0;
+  return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)RMAX, (size_t)nrhs), fit));
+}
+
 int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_params& prm, hdcg_stats* st,
           bool on_device) {
   HDCG_REQUIRE(nrhs >= 1, HDCG_ERR_ARG, "nrhs >= 1");
@@ -563,7 +605,8 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
     const double nreal = (double)c.n5 * 24.0;
     HDCG_CUDA(cudaMemcpyAsync(dsc(c, D_NREAL), &nreal, sizeof(double), cudaMemcpyHostToDevice, c.stream));
   }
-  const int chunk = prm.batch ? RMAX : 1;
+  const int chunk = batch_size(c, prm, nrhs, on_device);
+  st->batch_rhs = chunk;
   for (int k0 = 0; k0 < nrhs; k0 += chunk) {
     const int R = std::min(chunk, nrhs - k0);
     const char* bk = reinterpret_cast<const char*>(b) + k0 * canon;

@@ -34,6 +34,13 @@ class Workload:
     # coarse operator (~1e-6) is at the level of its FP32 rounding, so the
     # deflation's 1/lam factors are unreliable there; those workloads default to 0.
     ldop_nvec: int = 0
+    # set-up of the level-1 subspace: inverse-iteration steps, CG tolerance and
+    # iteration cap of each step; and of the level-2 subspace (three levels)
+    inv_steps: int = 3
+    inv_tol: float = 1e-4
+    inv_maxiter: int = 20000
+    inv2_steps: int = 2
+    inv2_tol: float = 1e-3
     extra: dict = field(default_factory=dict)
 
     @property
@@ -73,7 +80,8 @@ WORKLOADS = {
     # physical-point-like, three levels
     "cfg5_32x32x32x64_ls16_mobius_3lvl": Workload(
         "cfg5_32x32x32x64_ls16_mobius_3lvl", (32, 32, 32, 64), 16, 1.8, 1.5, 0.5, 0.001, 0.45,
-        (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=5),
+        (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=5,
+        inv_steps=2, inv_tol=1e-3, inv_maxiter=300),
     # Profiling case for the coarse level: the 24^3 x 48 coarse grid and Nvec of
     # cfg3 (an 860 MB FP16 little Dirac operator, larger than L2) over Ls = 2,
     # so the fine subspace stays near 1 GB.

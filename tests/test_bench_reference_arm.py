@@ -26,7 +26,7 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
     assert d["higher_is_better"] is False and d["value"] > 0 and d["unit"] == "s"
-    assert d["config"]["workload"].startswith("cfg2_16x16x16x16")
+    assert d["config"]["workload"].startswith("cfg5_32x32x32x64")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]

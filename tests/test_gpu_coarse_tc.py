@@ -2,7 +2,7 @@
 (hdcg_coarse_apply_multi): FP16 operators on the tensor cores (tcgen05), FP32
 operators on the tensor cores as FP16 hi + lo parts, FP64 operators on the
 CUDA cores, against the FP64 oracle's stencil apply
-y_a = sum_l A[a][l] x_{a+delta_l} (Sec. 4.3).
+y_a = sum_l A[a][l] x_{a+delta_l} (Sec. 5.1).
 
 The operator is a seeded random stencil rounded to the storage precision on
 the host (numpy) and uploaded with hdcg_set_coarse, so both sides apply the
