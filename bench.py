@@ -2,16 +2,18 @@
 with the fine Mpc^dag Mpc hop kernels' achieved bandwidth against the HBM roofline.
 
 One step = one full HDCG solve of H x = b to a true FP64 residual of ``tol``
-for all the workload's right-hand sides, inputs resident in HBM.  The default
-workload is the physical-point-like lattice: 32^3 x 64, Ls 16 Moebius
-(b 1.5, c 0.5), M5 1.8, m 0.001, links exp(i 0.45 H); 12 spin-colour point
-sources solved as a batch; three levels (4^4 blocks with Nvec 40, then 2^4
-blocks of the coarse lattice with Nvec 24); FP16 storage of the sloppy fine
-operator, the subspace and the little Dirac operator, FP32 outer operator,
-double-float (FP64-accurate) true residuals.  The subspaces and coarse
-operators are built once before the timed region (the paper reports set-up
-separately).  Inputs are larger than L2 (a 3.2 GB field per right-hand side)
-and L2 is flushed (a 512 MiB write) before every timed step anyway.
+(a Gaussian source; ``--nrhs`` of them together), inputs resident in HBM.  The
+default workload is the physical-point-like lattice: 32^3 x 64, Ls 16 Moebius
+(b 1.5, c 0.5), M5 1.8, m 0.001, links exp(i 0.45 H); three levels (4^4
+blocks with Nvec 40, then 2^4 blocks of the coarse lattice with Nvec 24);
+FP16 storage of the sloppy fine operator and the subspace, FP32 little Dirac
+operator, FP32 outer operator, double-float (FP64-accurate) true residuals.
+After the timed steps the workload's 12 spin-colour point sources are solved
+once as a batch (``batched``: time per right-hand side against the single
+solve).  The subspaces and coarse operators are built once before the timed
+region (the paper reports set-up separately).  Inputs are larger than L2 (a
+3.2 GB field per right-hand side) and L2 is flushed (a 512 MiB write) before
+every timed step anyway.
 
 Timed steps run with the library's event profiling off; the per-kernel
 profile (hop launch times and bytes, solve phases) comes from one extra
@@ -236,7 +238,7 @@ def run_reference(args, w):
         return
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(k, "1")
-    nrhs = args.nrhs or w.nrhs
+    nrhs = args.nrhs
     n_h = H_APPLIES_PER_RHS.get(w.name, 140)
     for _ in range(args.warmup):
         oracle_h_seconds_per_site(w)
@@ -260,7 +262,8 @@ def build_levels(h, w, seeds, args):
     """Subspaces and coarse operators (timed separately, outside the solves)."""
     prec = PREC[w.prec]
     sub_prec = prec if prec in (0, 1) else 2
-    coarse_prec = PREC[args.coarse_prec] if args.coarse_prec else (0 if prec == 0 else (1 if prec == 1 else 2))
+    cp = args.coarse_prec or w.coarse_prec
+    coarse_prec = PREC[cp] if cp else (0 if prec == 0 else (1 if prec == 1 else 2))
     out = {}
     t0 = time.perf_counter()
     h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=w.inv_steps, inv_shift=0.0, inv_tol=w.inv_tol,
@@ -309,7 +312,8 @@ def run_ours(args, w):
 
     prec = PREC[w.prec]
     outer = 0 if prec == 0 else 1
-    nrhs = args.nrhs or w.nrhs
+    nrhs = args.nrhs
+    batch_rhs = w.nrhs if args.batch_rhs is None else args.batch_rhs
     # the oracle's complete FP64 solve of the 8^4 x 8 workload runs on one host
     # core in a child process while the GPU works (about 1.5 minutes)
     oracle_proc = None
@@ -333,8 +337,12 @@ def run_ours(args, w):
     if nrhs == 1:
         bh = sy.gaussian_fermion(w.dims, w.Ls, seeds["source"])[None]
     else:
-        bh = sy.point_sources(w.dims, w.Ls, nrhs)
-    b = torch.from_numpy(bh).to(dev)
+        bh = sy.gaussian_fermions(w.dims, w.Ls, seeds["source"], nrhs)
+    # pinned host copies (the end-to-end run copies them in and out every step)
+    bp = torch.empty(bh.shape, dtype=torch.complex128, pin_memory=not args.no_e2e)
+    bp.numpy()[...] = bh
+    del bh
+    b = bp.to(dev)
     x = torch.zeros_like(b)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -385,19 +393,6 @@ def run_ours(args, w):
     # the solution's true residual, recomputed by the library's FP64-accurate operator
     true_res = s0["true_residual"]
 
-    # one right-hand side alone (the first), against the batch's time per right-hand side
-    single = None
-    if nrhs > 1:
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s1 = h.solve(b[:1].contiguous(), x[:1].contiguous(), w.tol, prm, nrhs=1).as_dict()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        single = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": s1["iterations"],
-                  "true_residual": s1["true_residual"], "batched_seconds_per_rhs": t_solve / nrhs}
 
     # plain red-black CG on the same GPU (FP32 with FP64 reliable updates), one
     # right-hand side, bounded by --cg-maxiter: if it has not converged by then,
@@ -425,14 +420,35 @@ def run_ours(args, w):
     del b, x
     torch.cuda.empty_cache()
 
+    # the batch of spin-colour point sources (12 for the physical-point-like
+    # workload), solved together in batches as large as the device memory takes
+    batched = None
+    if batch_rhs > 1:
+        pb = torch.from_numpy(sy.point_sources(w.dims, w.Ls, batch_rhs)).to(dev)
+        px = torch.zeros_like(pb)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sb = h.solve(pb, px, w.tol, prm, nrhs=batch_rhs).as_dict()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tb = e0.elapsed_time(e1) / 1e3
+        batched = {"rhs": batch_rhs, "sources": "spin-colour point sources", "seconds": tb,
+                   "seconds_per_rhs": tb / batch_rhs, "rhs_per_batch": sb["batch_rhs"],
+                   "iterations_max": sb["iterations"], "true_residual_max": sb["true_residual"],
+                   "status": sb["status"], "single_gaussian_rhs_seconds": t_solve / nrhs}
+        del pb, px
+        torch.cuda.empty_cache()
+
     # end to end through the public API with pinned host buffers (every step copies
     # the right-hand sides in and the solutions out)
     e2e = None
     if not args.no_e2e:
-        bp = torch.from_numpy(bh).pin_memory()
-        xp = torch.zeros_like(bp).pin_memory()
+        xp = torch.zeros(bp.shape, dtype=bp.dtype, pin_memory=True)
         ts_e2e = []
-        for _ in range(max(1, min(2, args.steps))):
+        for _ in range(1):
             flush.zero_()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -474,7 +490,8 @@ def run_ours(args, w):
                    "mass": w.mass, "eps": w.eps, "block": list(w.block), "nvec": w.nvec,
                    "block2": list(w.block2) if (w.block2 and not args.two_level) else None,
                    "nvec2": w.nvec2 if (w.block2 and not args.two_level) else None, "tol": w.tol,
-                   "storage": w.prec, "rhs_per_gpu": nrhs, "sources": "point" if nrhs > 1 else "gaussian",
+                   "storage": w.prec, "coarse_storage": args.coarse_prec or w.coarse_prec or w.prec,
+                   "rhs_per_gpu": nrhs, "sources": "gaussian",
                    "l2": "inputs larger than L2; also flushed (512 MiB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "roofline": None,
@@ -493,7 +510,7 @@ def run_ours(args, w):
                  "h_applies_per_rhs_reference_arm": H_APPLIES_PER_RHS.get(w.name)},
         "phases_ms_per_solve_profiled": phases,
         "hop_profile": hop_all,
-        "single_rhs": single,
+        "batched": batched,
         "setup_seconds": setup,
         "reliable_delta": args.reliable_delta,
     }
@@ -623,8 +640,10 @@ def main():
                     help="iteration cap of the plain-CG comparison (one right-hand side)")
     ap.add_argument("--coarse-prec", choices=["f64", "f32", "f16"], default=None,
                     help="storage of the little Dirac operator (default: the workload's)")
-    ap.add_argument("--nrhs", type=int, default=0,
-                    help="right-hand sides per solve (default: the workload's; reported as rhs_per_gpu)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="Gaussian right-hand sides per timed solve (reported as rhs_per_gpu)")
+    ap.add_argument("--batch-rhs", type=int, default=None,
+                    help="point sources of the one batched solve after the timed steps (default: the workload's)")
     ap.add_argument("--ldop-nvec", type=int, default=None,
                     help="second-level global deflation vectors (two-level workloads; default: the workload's)")
     ap.add_argument("--apply-only", type=int, default=0,

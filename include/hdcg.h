@@ -101,6 +101,19 @@ int hdcg_set_gauge(hdcg_t h, const void* U, int on_device);
  * precision prec on the device, distinct buffers.  Asynchronous on the stream. */
 int hdcg_apply_mpc(hdcg_t h, const void* in, void* out, int dagger, int prec);
 
+/* The full domain wall system D psi = eta on both checkerboards and its
+ * Schur-form reduction (Sec. 4): D = [[M_ee, M_eo], [M_oe, M_oo]] on (even, odd)
+ * sites, M_ee = M_oo = (4 - M5) K + 1 - P_s, M_eo = M_oe = -Dh K / 2.  The odd
+ * half of psi solves H psi_o = b with
+ *   b = Mpc^dag (eta_o - M_oe M_ee^-1 eta_e)          (hdcg_prep_source),
+ * and the even half is
+ *   psi_e = M_ee^-1 (eta_e - M_eo psi_o)              (hdcg_reconstruct).
+ * Every field is canonical complex double [cb][s][spin][colour] (the even
+ * field indexed by the even checkerboard, cb = lex >> 1 of its even sites),
+ * host or device (on_device), caller-owned.  FP64 arithmetic.  Synchronous. */
+int hdcg_prep_source(hdcg_t h, const void* eta_e, const void* eta_o, void* b, int on_device);
+int hdcg_reconstruct(hdcg_t h, const void* eta_e, const void* psi_o, void* psi_e, int on_device);
+
 /* out = H in = Mpc^dag Mpc in (Sec. 4).  If pHp is not NULL it receives
  * (in, H in) = |Mpc in|^2 accumulated in FP64 (then the call synchronises). */
 int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp);
@@ -230,6 +243,25 @@ int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, in
  * Synchronous: the call waits for its stream before returning. */
 int hdcg_coarse_apply_noalloc(hdcg_t h, const void* x, void* y);
 
+/* High-mode preconditioner of the little Dirac operator (Sec. 5.2, "Truncated
+ * little Dirac operator as preconditioner"; Table hierarchy: order 16 on
+ * [0.5, 45]): M = p(Q_trunc + shift), Q_trunc the blocks of A within one block
+ * hop (self and the eight nearest neighbours; on an extent of 2 the stored
+ * offsets only), p the Chebyshev-acceleration polynomial of degree order - 1
+ * on [lo, hi], 1 - x p(x) = T_order((theta - x)/delta) / T_order(theta/delta).
+ * hi <= 0 takes 1.1 times a power-iteration estimate of the largest eigenvalue
+ * of Q_trunc + shift (M is positive definite while that bound holds); lo <= 0
+ * takes hi |lo| (lo < 0) or hi / 90 (lo = 0, the paper's ratio).  interval
+ * (nullable, 2 doubles) receives [lo, hi].  From then on the level-1 solve
+ * with a level-2 operator smooths with M: y = z + Q2 (r - A z), z = M r.
+ * order 0 removes it; rebuilding A removes it too.  Needs an FP32 or FP16 A.
+ * Synchronous. */
+int hdcg_set_coarse_preconditioner(hdcg_t h, int order, double lo, double hi, double shift, double* interval);
+
+/* y = M x with the preconditioner above, nrhs (1..16) canonical coarse vectors
+ * [nrhs][Vc][Nvec] complex double on the device (FP32 arithmetic).  Synchronous. */
+int hdcg_coarse_precondition(hdcg_t h, const void* x, void* y, int nrhs);
+
 /* Second-level (global) deflation of the little Dirac operator (Sec. 5.2,
  * "Little Dirac operator deflation"): nvec Gaussian start vectors (splitmix64
  * stream seed, canonical order [k][Vc][Nvec], as for the subspace) refined by
@@ -288,6 +320,11 @@ typedef struct {
                               subspace and A once for all), as many per batch as the free
                               device memory takes (hdcg_stats.batch_rhs); 0 solves them one
                               after another */
+    int sloppy_codec;      /* the preconditioner's input (unit-RMS, 16-bit sloppy precision)
+                              passes through a reduced-precision codec of Sec. 6.5 before M_IRS,
+                              the precision of the paper's compressed preconditioner
+                              communication: 0 none, 1 each FP32 word truncated to 16 bits,
+                              2 8-bit integers with an FP16 prefactor per 5D site */
 } hdcg_params;
 
 typedef struct {
@@ -315,6 +352,15 @@ void hdcg_default_params(hdcg_params* p);
 int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p,
                hdcg_stats* st, int on_device);
 
+/* The 8-bit spinor codec of Sec. 6.5 (Table sloppy's proposal): every 5D site
+ * of nfields canonical odd fields (complex double, device) becomes an FP16
+ * prefactor p = fp16(max |real| of the site) (round to nearest even) and 24
+ * signed bytes q = clip(rint(127 v / p), -127, 127); decoding gives q p / 127.
+ * scale: [nfields][cb][s] IEEE half; q: [nfields][cb][s][24] int8 (the 24
+ * reals in canonical order).  FP64 arithmetic.  Asynchronous on the stream. */
+int hdcg_encode_i8(hdcg_t h, const void* in, void* scale, void* q, int nfields);
+int hdcg_decode_i8(hdcg_t h, const void* scale, const void* q, void* out, int nfields);
+
 /* ---------------------------------------------------------------------------
  * Instrumentation
  * ------------------------------------------------------------------------- */
@@ -333,6 +379,16 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
  * and r - H z), ms[2] FP64 true-residual H applies, ms[3] coarse CG, ms[4]
  * restriction and prolongation, ms[5] whole solves.  Synchronises the stream. */
 int hdcg_get_phase_profile(hdcg_t h, double ms[6]);
+/* The fine operator's hop passes come in variants: 0-2 scalar FP32 arithmetic
+ * with register budgets for 1, 2 and 3 resident CTAs per SM; 3 all eight
+ * neighbours prefetched (16-bit storage) or double-float arithmetic (FP64
+ * storage); 4 and 5 packed FP32 (f32x2) arithmetic with the links staged in
+ * shared memory (FP32 and 16-bit storage).  By default (variant -1) the first
+ * launch of each pass times the variants and keeps the fastest; 0..5 forces
+ * one (for FP64 storage variants 4 and 5 fall back to 0).  HDCG_ERR_ARG
+ * outside -1..5. */
+int hdcg_set_hop_variant(hdcg_t h, int variant);
+
 /* Count of library kernel launches issued on the handle since creation. */
 long long hdcg_launch_count(hdcg_t h);
 

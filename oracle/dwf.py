@@ -236,6 +236,30 @@ class DWF:
         """H psi = Mpc^dag Mpc psi."""
         return self.mpc_dag(self.mpc(psi))
 
+    # -- the full (unpreconditioned) system and its Schur-form reduction (Sec. 4) --
+    # D = [[M_ee, M_eo], [M_oe, M_oo]] on (even, odd) sites with
+    # M_ee = M_oo = (4 - M5) K + 1 - P_s and M_eo, M_oe = -1/2 Dh K.
+
+    def apply_full(self, psi_e, psi_o):
+        """(eta_e, eta_o) = D (psi_e, psi_o)."""
+        S = self.S
+        eta_e = apply_s(S["Mee"], psi_e) - 0.5 * self._hop(apply_s(S["K"], psi_o), 0)
+        eta_o = apply_s(S["Mee"], psi_o) - 0.5 * self._hop(apply_s(S["K"], psi_e), 1)
+        return eta_e, eta_o
+
+    def prep_source(self, eta_e, eta_o):
+        """b = Mpc^dag (eta_o - M_oe M_ee^-1 eta_e): the right-hand side of the
+        odd-site normal equation H psi_o = b whose solution is the odd half of
+        D psi = eta."""
+        S = self.S
+        eta_p = eta_o + 0.5 * self._hop(apply_s(S["K"], apply_s(S["Meeinv"], eta_e)), 1)
+        return self.mpc_dag(eta_p)
+
+    def reconstruct(self, eta_e, psi_o):
+        """psi_e = M_ee^-1 (eta_e - M_eo psi_o), the even half of the solution."""
+        S = self.S
+        return apply_s(S["Meeinv"], eta_e + 0.5 * self._hop(apply_s(S["K"], psi_o), 0))
+
     def mdagm_shift(self, psi, shift):
         return self.mdagm(psi) + shift * psi
 

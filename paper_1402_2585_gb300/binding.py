@@ -42,7 +42,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int), ("outer_prec", ctypes.c_int), ("sloppy_prec", ctypes.c_int),
                 ("mirs_iter", ctypes.c_int), ("mirs_shift", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxiter", ctypes.c_int), ("flexible", ctypes.c_int), ("maxiter", ctypes.c_int),
-                ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int)]
+                ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int), ("sloppy_codec", ctypes.c_int)]
 
 
 class LdopParams(ctypes.Structure):
@@ -70,6 +70,8 @@ _SIGS = {
     "hdcg_set_gauge": (_I, [_P, _P, _I]),
     "hdcg_apply_mpc": (_I, [_P, _P, _P, _I, _I]),
     "hdcg_apply_mdagm": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "hdcg_prep_source": (_I, [_P, _P, _P, _P, _I]),
+    "hdcg_reconstruct": (_I, [_P, _P, _P, _P, _I]),
     "hdcg_build_subspace": (_I, [_P, ctypes.POINTER(SubspaceParams)]),
     "hdcg_set_subspace": (_I, [_P, _I, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
     "hdcg_get_subspace": (_I, [_P, _I, _P]),
@@ -85,6 +87,8 @@ _SIGS = {
     "hdcg_coarse_apply_multi": (_I, [_P, _P, _P, _I]),
     "hdcg_coarse_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(_I)]),
     "hdcg_build_coarse_deflation": (_I, [_P, ctypes.POINTER(LdopParams)]),
+    "hdcg_set_coarse_preconditioner": (_I, [_P, _I, _D, _D, _D, ctypes.POINTER(_D)]),
+    "hdcg_coarse_precondition": (_I, [_P, _P, _P, _I]),
     "hdcg_get_coarse_deflation": (_I, [_P, ctypes.POINTER(_D), _P]),
     "hdcg_dense_heev": (_I, [_I, _P, _P, _P]),
     "hdcg_default_params": (None, [ctypes.POINTER(SolveParams)]),
@@ -94,6 +98,9 @@ _SIGS = {
                                   ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "hdcg_get_phase_profile": (_I, [_P, ctypes.POINTER(_D)]),
     "hdcg_launch_count": (ctypes.c_longlong, [_P]),
+    "hdcg_set_hop_variant": (_I, [_P, _I]),
+    "hdcg_encode_i8": (_I, [_P, _P, _P, _P, _I]),
+    "hdcg_decode_i8": (_I, [_P, _P, _P, _P, _I]),
     "hdcg_last_error": (ctypes.c_char_p, [_P]),
     "hdcg_destroy": (None, [_P]),
     "hdcg_version": (_I, []),
@@ -197,6 +204,13 @@ class Hdcg:
                                              ctypes.byref(v) if want_pHp else None))
         return v.value if want_pHp else None
 
+    def prep_source(self, eta_e, eta_o, b):
+        return self._check(self._L.hdcg_prep_source(self.h, _ptr(eta_e), _ptr(eta_o), _ptr(b), _on_device(b)))
+
+    def reconstruct(self, eta_e, psi_o, psi_e):
+        return self._check(self._L.hdcg_reconstruct(self.h, _ptr(eta_e), _ptr(psi_o), _ptr(psi_e),
+                                                     _on_device(psi_e)))
+
     # -- subspace and coarse operator -----------------------------------------
     def build_subspace(self, block, nvec, prec=F32, inv_steps=3, inv_shift=0.0, inv_tol=1e-4,
                        inv_maxiter=20000, seed=0, level=1):
@@ -244,6 +258,15 @@ class Hdcg:
         self._check(self._L.hdcg_coarse_solve(self.h, _ptr(b), _ptr(x), int(nrhs), float(tol), int(maxiter),
                                                ctypes.byref(it)))
         return it.value
+
+    def set_coarse_preconditioner(self, order, lo=0.0, hi=0.0, shift=0.0):
+        """Chebyshev preconditioner of Q_trunc; returns the interval (lo, hi) used."""
+        iv = (ctypes.c_double * 2)()
+        self._check(self._L.hdcg_set_coarse_preconditioner(self.h, int(order), float(lo), float(hi), float(shift), iv))
+        return iv[0], iv[1]
+
+    def coarse_precondition(self, x, y, nrhs=1):
+        return self._check(self._L.hdcg_coarse_precondition(self.h, _ptr(x), _ptr(y), int(nrhs)))
 
     def build_coarse_deflation(self, nvec, inv_steps=3, shift=0.0, tol=1e-7, maxiter=100000, seed=0):
         p = LdopParams(int(nvec), int(inv_steps), float(shift), float(tol), int(maxiter), int(seed))
@@ -296,6 +319,15 @@ class Hdcg:
         ms = (ctypes.c_double * 6)()
         self._check(self._L.hdcg_get_phase_profile(self.h, ms))
         return dict(zip(self.PHASES, list(ms)))
+
+    def encode_i8(self, x, scale, q, nfields=1):
+        return self._check(self._L.hdcg_encode_i8(self.h, _ptr(x), _ptr(scale), _ptr(q), int(nfields)))
+
+    def decode_i8(self, scale, q, x, nfields=1):
+        return self._check(self._L.hdcg_decode_i8(self.h, _ptr(scale), _ptr(q), _ptr(x), int(nfields)))
+
+    def set_hop_variant(self, variant):
+        return self._check(self._L.hdcg_set_hop_variant(self.h, int(variant)))
 
     def launch_count(self):
         return int(self._L.hdcg_launch_count(self.h))

@@ -68,4 +68,11 @@ void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, cons
 // y = sqrt(num/den)^(inv ? -1 : 1) x
 void scale_dev(Ctx& c, int prec, const uint4* x, uint4* y, const double* num, const double* den, int inv);
 
+// reduced-precision codecs of Sec. 6.5 (codec.cu): canonical complex double
+// fields <-> (FP16 prefactor per 5D site, 24 int8 per site); and the solver's
+// in-place round trip of an internal field (codec 1: 16-bit truncation, 2: 8-bit)
+void encode_i8(Ctx& c, const void* in, void* scale, void* q, size_t nfields);
+void decode_i8(Ctx& c, const void* scale, const void* q, void* out, size_t nfields);
+void codec_roundtrip(Ctx& c, uint4* f, int prec, int codec, int nrhs = 1);
+
 }  // namespace hdcg

@@ -13,6 +13,8 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
           bool on_device);
 void build_subspace(Ctx& c, const hdcg_subspace_params& p);
 void build_coarse(Ctx& c, int prec);
+void prep_source(Ctx& c, const void* eta_e, const void* eta_o, void* b);
+void reconstruct(Ctx& c, const void* eta_e, const void* psi_o, void* psi_e);
 void set_coarse(Ctx& c, const void* A, int prec, int on_device);
 
 static void resolve_profile(Ctx& c) {
@@ -187,6 +189,61 @@ int hdcg_apply_mdagm(hdcg_t h, const void* in, void* out, int prec, double* pHp)
 
 static void check_level(int level) {
   HDCG_REQUIRE(level == 1 || level == 2, HDCG_ERR_ARG, "level must be 1 (fine lattice) or 2 (coarse lattice)");
+}
+
+// stage up to three canonical complex double fields through the device when
+// the caller's buffers are on the host
+struct HostFields {
+  Ctx& c;
+  DevMem d[3];
+  explicit HostFields(Ctx& c_) : c(c_) {}
+  const void* in(int i, const void* p, int on_device) {
+    if (on_device) return p;
+    const size_t bytes = c.n5 * 12 * sizeof(double2);
+    d[i].ensure(bytes);
+    HDCG_CUDA(cudaMemcpyAsync(d[i].p, p, bytes, cudaMemcpyHostToDevice, c.stream));
+    return d[i].p;
+  }
+  void* out(int i, void* p, int on_device) {
+    if (on_device) return p;
+    d[i].ensure(c.n5 * 12 * sizeof(double2));
+    return d[i].p;
+  }
+  void back(int i, void* p, int on_device) {
+    if (!on_device)
+      HDCG_CUDA(cudaMemcpyAsync(p, d[i].p, c.n5 * 12 * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+    HDCG_CUDA(cudaStreamSynchronize(c.stream));
+  }
+};
+
+int hdcg_prep_source(hdcg_t h, const void* eta_e, const void* eta_o, void* b, int on_device) {
+  HDCG_ENTRY(h, {
+    check_ptr(eta_e, "eta_e");
+    check_ptr(eta_o, "eta_o");
+    check_ptr(b, "b");
+    HostFields hf(c);
+    const void* e = hf.in(0, eta_e, on_device);
+    const void* o = hf.in(1, eta_o, on_device);
+    void* bo = hf.out(2, b, on_device);
+    prep_source(c, e, o, bo);
+    hf.back(2, b, on_device);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_reconstruct(hdcg_t h, const void* eta_e, const void* psi_o, void* psi_e, int on_device) {
+  HDCG_ENTRY(h, {
+    check_ptr(eta_e, "eta_e");
+    check_ptr(psi_o, "psi_o");
+    check_ptr(psi_e, "psi_e");
+    HostFields hf(c);
+    const void* e = hf.in(0, eta_e, on_device);
+    const void* o = hf.in(1, psi_o, on_device);
+    void* pe = hf.out(2, psi_e, on_device);
+    reconstruct(c, e, o, pe);
+    hf.back(2, psi_e, on_device);
+  });
+  return HDCG_OK;
 }
 
 int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p) {
@@ -389,6 +446,30 @@ int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, in
   return HDCG_OK;
 }
 
+int hdcg_set_coarse_preconditioner(hdcg_t h, int order, double lo, double hi, double shift, double* interval) {
+  HDCG_ENTRY(h, {
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    HDCG_REQUIRE(order >= 0 && order <= 256, HDCG_ERR_ARG, "order must be 0..256");
+    HDCG_REQUIRE(std::isfinite(lo) && std::isfinite(hi) && std::isfinite(shift), HDCG_ERR_ARG, "non-finite argument");
+    qtrunc_setup(c, *c.coarse, order, lo, hi, shift);
+    if (interval) {
+      interval[0] = c.coarse->qt.lo;
+      interval[1] = c.coarse->qt.hi;
+    }
+  });
+  return HDCG_OK;
+}
+
+int hdcg_coarse_precondition(hdcg_t h, const void* x, void* y, int nrhs) {
+  HDCG_ENTRY(h, {
+    check_ptr(x, "x");
+    check_ptr(y, "y");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    qtrunc_precondition_canon(c, *c.coarse, nrhs, x, y);
+  });
+  return HDCG_OK;
+}
+
 int hdcg_build_coarse_deflation(hdcg_t h, const hdcg_ldop_params* p) {
   HDCG_ENTRY(h, {
     check_ptr(p, "params");
@@ -441,6 +522,7 @@ void hdcg_default_params(hdcg_params* p) {
   p->maxiter = 10000;
   p->reliable_delta = 0.01;
   p->batch = 1;
+  p->sloppy_codec = 0;
 }
 
 int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p, hdcg_stats* st,
@@ -501,6 +583,36 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
     if (total_ms) *total_ms = c.prof.ms[prec];
     if (bytes) *bytes = c.prof.bytes[prec];
     if (op_bytes) *op_bytes = c.prof.op_bytes[prec];
+  });
+  return HDCG_OK;
+}
+
+int hdcg_encode_i8(hdcg_t h, const void* in, void* scale, void* q, int nfields) {
+  HDCG_ENTRY(h, {
+    check_ptr(in, "in");
+    check_ptr(scale, "scale");
+    check_ptr(q, "q");
+    HDCG_REQUIRE(nfields >= 1, HDCG_ERR_ARG, "nfields >= 1");
+    encode_i8(c, in, scale, q, nfields);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_decode_i8(hdcg_t h, const void* scale, const void* q, void* out, int nfields) {
+  HDCG_ENTRY(h, {
+    check_ptr(out, "out");
+    check_ptr(scale, "scale");
+    check_ptr(q, "q");
+    HDCG_REQUIRE(nfields >= 1, HDCG_ERR_ARG, "nfields >= 1");
+    decode_i8(c, scale, q, out, nfields);
+  });
+  return HDCG_OK;
+}
+
+int hdcg_set_hop_variant(hdcg_t h, int variant) {
+  HDCG_ENTRY(h, {
+    HDCG_REQUIRE(variant >= -1 && variant <= 5, HDCG_ERR_ARG, "hop variant must be -1..5");
+    c.hop_force = variant;
   });
   return HDCG_OK;
 }

@@ -597,6 +597,7 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   A.graph_cg.reset();
   A.graph_ad1.reset();
   A.Aacc.release();
+  A.qt.order = 0;           // the preconditioner belongs to the operator it was built from
   // a level-2 subspace of the same geometry is kept (subspace reuse); its
   // operator belongs to the old A and is rebuilt with hdcg_build_coarse(level 2)
   if (A.l2 && (A.l2->Vc1 != s.Vc || A.l2->n1 != s.nvec)) {

@@ -46,6 +46,17 @@ struct Level2 {
   CapturedGraph graph;
 };
 
+// high-mode preconditioner of the little Dirac operator (qtrunc.cu): a
+// Chebyshev polynomial of the 9-block truncation Q_trunc of A (Sec. 5.2)
+struct QTrunc {
+  int order = 0;            // 0: none (M = 1)
+  int nq = 0;               // kept blocks per coarse site (<= 9)
+  double lo = 0, hi = 0, shift = 0;
+  DevMem A9;                // [Vc][9][k][j] complex float (the kept blocks of A)
+  DevMem nb9;               // int32 [Vc][9]
+  DevMem work;              // Chebyshev vectors
+};
+
 struct Coarse {
   int prec = HDCG_F32;      // storage of A (F64, F32 or F16); vectors: F64 if A is F64 else F32
   int nvec = 0;
@@ -75,6 +86,7 @@ struct Coarse {
   // level-2 operator is contracted
   DevMem Aacc;
   Level2* l2 = nullptr;
+  QTrunc qt;
   Coarse() = default;
   Coarse(const Coarse&) = delete;
   Coarse& operator=(const Coarse&) = delete;
@@ -133,6 +145,14 @@ void level2_prolong_canon(Ctx& c, const Coarse& A, int R, const void* c64, void*
 bool level2_active(const Coarse& A);
 // level-1 solve A x = b (FP32 [e][r]) by A-DEF2 with Q2 = P2 A2^-1 R2; returns iterations
 int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double tol, int maxiter);
+
+// Chebyshev preconditioner of Q_trunc (qtrunc.cu): set up (order 0 removes it;
+// hi <= 0: 1.1 x the power-iteration estimate of lambda_max(Q_trunc + shift);
+// lo <= 0: hi |lo|, or hi / 90 for lo = 0), apply to FP32 [e][r] vectors
+void qtrunc_setup(Ctx& c, Coarse& A, int order, double lo, double hi, double shift);
+void qtrunc_apply(Ctx& c, const Coarse& A, int R, const float2* x, float2* y, double shift, const int* skip);
+void qtrunc_precondition(Ctx& c, Coarse& A, int R, const float2* r, float2* y, unsigned* xm, const int* skip);
+void qtrunc_precondition_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y64);
 
 // subspace geometry (host tables -> device)
 void subspace_init(Ctx& c, Subspace& s, const int block[4], int nvec, int prec);

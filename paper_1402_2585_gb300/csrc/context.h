@@ -118,6 +118,7 @@ struct Ctx {
   DevMem scratch_f[NPREC][24]; // work fields per precision (slot roles: solver.cu; 20-23: hop autotuner)
   std::map<int, int> hop_tuned;  // (prec, pass, fused, reduction) -> chosen hop variant
   bool tuning_off = false;
+  int hop_force = -1;            // >= 0: every hop launch uses this variant (hdcg_set_hop_variant)
   DevMem red_partials, red_ticket, scalars;
   DevMem canon_in, canon_out;  // canonical <-> internal staging
 

@@ -195,6 +195,12 @@ static void dispatch_hop(int prec, int v, int pass, bool mob, const HopArgs& a, 
 // caller's data, so in-place CG updates are not repeated) and keeps the fastest.
 static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, dim3 grid) {
   const int key = ((prec * 4 + pass) * 2 + (a.cg_r ? 1 : 0)) * 2 + (a.do_red ? 1 : 0);
+  if (c.hop_force >= 0) {
+    // a forced variant (hdcg_set_hop_variant); the packed variants exist for
+    // FP32 and 16-bit storage only
+    const bool wide = prec == HDCG_F64 || prec == HDCG_DF64;
+    return (wide && c.hop_force >= 4) ? 0 : c.hop_force;
+  }
   auto it = c.hop_tuned.find(key);
   if (it != c.hop_tuned.end()) return it->second;
   if (c.tuning_off) {
@@ -229,7 +235,8 @@ static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, d
   HDCG_CUDA(cudaEventCreate(&e1));
   int best = 0;
   float best_ms = 1e30f;
-  for (int v = 0; v < HOP_VARIANTS; ++v) {
+  const int nv = (prec == HDCG_F64 || prec == HDCG_DF64) ? 4 : HOP_VARIANTS;
+  for (int v = 0; v < nv; ++v) {
     dispatch_hop(prec, v, pass, mob, t, grid, c.stream);  // warm-up
     HDCG_CUDA(cudaEventRecord(e0, c.stream));
     for (int r = 0; r < 3; ++r) dispatch_hop(prec, v, pass, mob, t, grid, c.stream);
@@ -245,8 +252,11 @@ static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, d
   HDCG_CUDA(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c.launches += 4 * HOP_VARIANTS;
+  c.launches += 4 * nv;
   c.hop_tuned[key] = best;
+  // the timing fields are temporary: give their memory back (3.2 GB each for a
+  // 32^3 x 64 x 16 FP64 field)
+  for (int i = 20; i < 24; ++i) c.scratch_f[prec][i].release();
   return best;
 }
 

@@ -502,13 +502,44 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
 }
 
 
-// MINB = 1, 2, 3; 4th (MINB 1): prefetch of all neighbours for 16-bit storage,
-// double-float arithmetic for FP64 storage
-constexpr int HOP_VARIANTS = 4;
+}  // namespace hdcg
 
-// launch variant v (0..3) of one pass for storage St
+#include "hop_packed.cuh"
+
+namespace hdcg {
+
+// MINB = 1, 2, 3; 4th (MINB 1): prefetch of all neighbours for 16-bit storage,
+// double-float arithmetic for FP64 storage; 5th and 6th (FP32 and 16-bit
+// storage only): packed FP32 arithmetic (hop_packed.cuh) with MINB 2 and 1
+constexpr int HOP_VARIANTS = 6;
+template <typename St> constexpr int hop_variants() { return Store<St>::chunks == 12 ? 4 : 6; }
+
+// launch variant v of one pass for storage St
 template <typename St>
 void launch_hop_variant(int v, int pass, bool mob, const HopArgs& a, dim3 grid, cudaStream_t st) {
+  if constexpr (Store<St>::chunks != 12) {
+    if (v >= 4) {
+      const bool stage = a.Ls >= 8;
+#define HDCG_HOP_PK(P, M)                                                                       \
+      if (pass == P) {                                                                         \
+        if (stage) {                                                                           \
+          if (mob) pk::hop_packed_kernel<St, P, true, M, true><<<grid, 256, 0, st>>>(a);       \
+          else pk::hop_packed_kernel<St, P, false, M, true><<<grid, 256, 0, st>>>(a);          \
+        } else {                                                                               \
+          if (mob) pk::hop_packed_kernel<St, P, true, M, false><<<grid, 256, 0, st>>>(a);      \
+          else pk::hop_packed_kernel<St, P, false, M, false><<<grid, 256, 0, st>>>(a);         \
+        }                                                                                      \
+        return;                                                                                \
+      }
+      if (v == 4) {
+        HDCG_HOP_PK(PASS_A, 2) HDCG_HOP_PK(PASS_B, 2) HDCG_HOP_PK(PASS_C, 2) HDCG_HOP_PK(PASS_D, 2)
+      } else {
+        HDCG_HOP_PK(PASS_A, 1) HDCG_HOP_PK(PASS_B, 1) HDCG_HOP_PK(PASS_C, 1) HDCG_HOP_PK(PASS_D, 1)
+      }
+#undef HDCG_HOP_PK
+      return;
+    }
+  }
 #define HDCG_HOP_CASE(P, M)                                                      \
   if (pass == P && v == M - 1) {                                                 \
     if (mob) hop_kernel<St, P, true, M><<<grid, 256, 0, st>>>(a);               \

@@ -181,12 +181,13 @@ __global__ void __launch_bounds__(256) k_l2_restrict(const float2* __restrict__ 
   }
 }
 
-// y[e][r] = (add ? add[e][r] : 0) + sum_k phi_k[e] c2[b(e)][k][r]; with dot != null the
-// per-right-hand-side Re<add, y> (add = r in the level-1 solver: (r, y)) is reduced into it
+// y[e][r] = (add ? add[e][r] : 0) + sum_k phi_k[e] c2[b(e)][k][r]; with want_dot the
+// per-right-hand-side Re<dv, y> is reduced (dv = r in the level-1 solver: (r, y))
 __global__ void __launch_bounds__(256) k_l2_prolong(const float2* __restrict__ phi, size_t ne, int nv, int n1,
                                                     const int* __restrict__ blk, const float2* __restrict__ c2,
                                                     int R, const float2* __restrict__ add, float2* y,
-                                                    const int* skip, Reduction red, int want_dot) {
+                                                    const int* skip, Reduction red, int want_dot,
+                                                    const float2* __restrict__ dv) {
   if (skip && *skip) return;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   float ar[RMAX], ai[RMAX];
@@ -215,6 +216,9 @@ __global__ void __launch_bounds__(256) k_l2_prolong(const float2* __restrict__ p
           const float2 s = add[e * R + q];
           o.x += s.x;
           o.y += s.y;
+        }
+        if (want_dot) {
+          const float2 s = dv[e * R + q];
           v[q] = (double)s.x * o.x + (double)s.y * o.y;
         }
         y[e * R + q] = o;
@@ -590,7 +594,7 @@ struct CtlL2 {
   double ry[2][RMAX];       // (r, y) by parity
   double stop[RMAX];
   int done[RMAX];
-  unsigned xm[2][RMAX];     // max |Re|, |Im| of p (0) and r (1): tensor-core operand scales
+  unsigned xm[3][RMAX];     // max |Re|, |Im| of p (0), r (1) and M r (2): tensor-core operand scales
   int iter;
   int all_done;
 };
@@ -1028,12 +1032,12 @@ static void l2_restrict(Ctx& c, const Level2& L, const float2* x, const float2* 
   ++c.launches;
 }
 static void l2_prolong(Ctx& c, const Level2& L, const float2* c2, int R, const float2* add, float2* y,
-                       const int* skip, double* dot) {
+                       const int* skip, double* dot, const float2* dv = nullptr) {
   const size_t ne = L.Vc1 * L.n1;
   const unsigned g = nblocks(ne);
   const Reduction red = dot ? make_reduction(c, g, RMAX, dot, 0) : Reduction{};
   k_l2_prolong<<<g, 256, 0, c.stream>>>(L.phi.as<float2>(), ne, L.nvec, L.n1, L.blk_of_site.as<int>(), c2, R, add, y,
-                                        skip, red, dot ? 1 : 0);
+                                        skip, red, dot ? 1 : 0, dv ? dv : add);
   ++c.launches;
 }
 static void l2_dense_solve(Ctx& c, const Level2& L, const float2* t, int R, float2* u, const int* skip) {
@@ -1092,7 +1096,7 @@ int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
   coarse_tc_prepare(c, A);
   Level2& L = *A.l2;
   const size_t ne = L.Vc1 * L.n1, nc = ne * R, n2 = L.Vc2 * L.nvec * R;
-  L.work.ensure((4 * nc + 2 * n2) * sizeof(float2));
+  L.work.ensure((5 * nc + 2 * n2) * sizeof(float2));
   L.ctl.ensure(sizeof(CtlL2));
   float2* r = L.work.as<float2>();
   float2* p = r + nc;
@@ -1100,6 +1104,7 @@ int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
   float2* y = w + nc;
   float2* c2 = y + nc;
   float2* u2 = c2 + n2;
+  float2* zb = u2 + n2;      // M r (with the Q_trunc preconditioner)
   const float2* b = (const float2*)rhs;
   float2* x = (float2*)sol;
   CtlL2* ctl = L.ctl.as<CtlL2>();
@@ -1118,12 +1123,21 @@ int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
   k_l1_residual<<<ge, 256, 0, c.stream>>>(b, w, r, ne, R, ctl->xm[1], make_reduction(c, ge, RMAX, ctl->rr, 0));
   k_l1_start<<<1, 1, 0, c.stream>>>(ctl, R, tol, maxiter);
   c.launches += 2;
-  // y = M1 r = r + Q2 (r - A r), (r, y) into ry[par]; w is scratch for A r
+  // y = M1 r = z + Q2 (r - A z) with z = M r (M = 1, or the Chebyshev
+  // polynomial of Q_trunc), (r, y) into ry[par]; w is scratch for A z
+  const bool smooth = A.qt.order > 0;
   auto M1 = [&](int par) {
-    l1_apply(c, A, R, r, w, ctl->xm[1], skip, nullptr);
+    const float2* z = r;
+    const unsigned* xz = ctl->xm[1];
+    if (smooth) {
+      qtrunc_precondition(c, A, R, r, zb, ctl->xm[2], skip);
+      z = zb;
+      xz = ctl->xm[2];
+    }
+    l1_apply(c, A, R, z, w, xz, skip, nullptr);
     l2_restrict(c, L, r, w, R, c2, skip);
     l2_dense_solve(c, L, c2, R, u2, skip);
-    l2_prolong(c, L, u2, R, r, y, skip, ctl->ry[par]);
+    l2_prolong(c, L, u2, R, z, y, skip, ctl->ry[par], r);
   };
   M1(0);
   k_l1_p<<<ge, 256, 0, c.stream>>>(p, y, ne, R, ctl, 0, 1);
@@ -1142,7 +1156,8 @@ int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
   const std::vector<uintptr_t> key = {(uintptr_t)L.work.p, (uintptr_t)L.ctl.p, (uintptr_t)sol, (uintptr_t)rhs,
                                       (uintptr_t)A.Atc.p, (uintptr_t)A.xtc.p, (uintptr_t)A.tcs.p,
                                       (uintptr_t)L.Ainv.p, (uintptr_t)c.red_partials.p, (uintptr_t)c.red_ticket.p,
-                                      (uintptr_t)R, (uintptr_t)maxiter};
+                                      (uintptr_t)R, (uintptr_t)maxiter, (uintptr_t)A.qt.order,
+                                      (uintptr_t)A.qt.work.p, (uintptr_t)A.qt.A9.p};
   int queued = 0;
   int batch = std::max(2, L.last_iters);
   CtlL2 h{};

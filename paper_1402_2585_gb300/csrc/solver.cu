@@ -157,6 +157,10 @@ static void apply_M1(Ctx& c, int op, int sp, const uint4* r, uint4* y, const hdc
     convert_field(c, r, op, t, sp);
     rs = t;
   }
+  if (prm.sloppy_codec) {
+    HDCG_REQUIRE(scaled, HDCG_ERR_ARG, "sloppy_codec needs a 16-bit sloppy precision (unit-RMS input)");
+    codec_roundtrip(c, const_cast<uint4*>(rs), sp, prm.sloppy_codec);
+  }
   uint4* z = c.scratch(sp, SL_Z);
   uint4* t = c.scratch(sp, SL_T);
   int nm = 0;
@@ -384,6 +388,10 @@ static void apply_M1_multi(Ctx& c, int op, int sp, int R, const uint4* r, uint4*
     convert_field(c, r, op, t, sp, R);
     rs = t;
   }
+  if (prm.sloppy_codec) {
+    HDCG_REQUIRE(scaled, HDCG_ERR_ARG, "sloppy_codec needs a 16-bit sloppy precision (unit-RMS input)");
+    codec_roundtrip(c, const_cast<uint4*>(rs), sp, prm.sloppy_codec, R);
+  }
   uint4* z = c.scratch(sp, SL_Z, R);
   int nm = 0;
   uint4* t;
@@ -583,10 +591,21 @@ static int batch_size(Ctx& c, const hdcg_params& prm, int nrhs, bool on_device) 
   if (!prm.batch) return 1;
   size_t freeb = 0, total = 0;
   HDCG_CUDA(cudaMemGetInfo(&freeb, &total));
-  size_t held = c.canon_in.bytes + c.canon_out.bytes;
-  for (int p = 0; p < NPREC; ++p)
-    for (int i = 0; i < 20; ++i) held += c.scratch_f[p][i].bytes;
-  const size_t avail = freeb + held, reserve = size_t(4) << 30;
+  // work fields that grow with the batch (and are reused by it when they exist)
+  const int op = prm.outer_prec, sp = prm.sloppy_prec;
+  size_t held = on_device ? 0 : c.canon_in.bytes + c.canon_out.bytes;
+  for (int slot : {(int)SL_B, (int)SL_XHI}) held += c.scratch_f[HDCG_F64][slot].bytes;
+  for (int slot : {(int)SL_XLO, (int)SL_R, (int)SL_P, (int)SL_Y, 0, 1}) held += c.scratch_f[op][slot].bytes;
+  if (prm.algorithm == HDCG_ALG_ADEF2 && sp != op)
+    for (int slot : {(int)SL_RS, (int)SL_Z, (int)SL_MRES, (int)SL_MP, 0, 1}) held += c.scratch_f[sp][slot].bytes;
+  // fields that do not grow with the batch but may not exist yet: the
+  // double-float residual (five fields), the FP64 residual, the hop autotuner's
+  // four temporary fields
+  size_t fixed = 0;
+  if (!c.scratch_f[HDCG_DF64][5].p) fixed += 5 * c.field_bytes(HDCG_DF64) + c.field_bytes(HDCG_F64);
+  fixed += 4 * c.field_bytes(HDCG_DF64);
+  const size_t reserve = (size_t(4) << 30) + fixed;
+  const size_t avail = freeb + held;
   const size_t per = bytes_per_rhs(c, prm, on_device);
   const size_t fit = avail > reserve ? (avail - reserve) / per : 0;
   return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)RMAX, (size_t)nrhs), fit));

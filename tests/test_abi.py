@@ -17,7 +17,8 @@ def test_header_declares_the_boundary():
     for n in ["hdcg_create", "hdcg_set_dwf", "hdcg_set_gauge", "hdcg_apply_mpc", "hdcg_apply_mdagm",
               "hdcg_build_subspace", "hdcg_set_subspace", "hdcg_build_coarse", "hdcg_get_coarse",
               "hdcg_restrict", "hdcg_prolong", "hdcg_coarse_apply", "hdcg_solve", "hdcg_last_error",
-              "hdcg_destroy"]:
+              "hdcg_destroy", "hdcg_prep_source", "hdcg_reconstruct", "hdcg_restrict_coarse",
+              "hdcg_prolong_coarse"]:
         assert n in names
 
 

@@ -103,3 +103,44 @@ def test_argument_errors():
     h2 = Hdcg((4, 4, 4, 4), 4)
     with pytest.raises(HdcgError):
         h2.apply_mpc(x, torch.empty_like(x), prec=F32)   # no gauge field yet
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("prec", [F32, F16, BF16T])
+def test_every_hop_variant(case, variant, prec):
+    """Each kernel variant the hop autotuner can choose (forced with
+    hdcg_set_hop_variant): the scalar register-budget variants, the prefetching
+    one, and the packed-FP32 ones with links staged in shared memory (Ls >= 8)
+    or expanded per thread (Ls < 8); same bars as above."""
+    torch, d, h = _setup(case, seed=1)
+    h.set_hop_variant(variant)
+    psi = sy.gaussian_fermion(d.lat.dims, d.Ls, 610)
+    x = to_gpu(psi, prec)
+    y = torch.empty_like(x)
+    for dagger, ref in ((False, d.mpc), (True, d.mpc_dag)):
+        h.apply_mpc(x, y, dagger=dagger, prec=prec)
+        assert rel(from_gpu(y), ref(psi)) < TOL[prec]
+    pHp = h.apply_mdagm(x, y, prec=prec, want_pHp=True)
+    assert rel(from_gpu(y), d.mdagm(psi)) < TOL[prec]
+    assert pHp == pytest.approx(norm2(d.mpc(psi)), rel=TOL[prec])
+
+
+@pytest.mark.parametrize("variant", [0, 4, 5])
+def test_fused_cg_step_every_variant(variant):
+    """The CG step fused into the last hop pass (x += alpha p, r -= alpha H p,
+    |r|^2) in each variant: a plain FP32 CG solve reaches the oracle's true
+    residual and solution (kappa ~ 1e2 on this lattice)."""
+    from oracle.solvers import cg
+    from paper_1402_2585_gb300 import ALG_CG
+    torch, d, h = _setup("mobius_8x4x4x6_ls8_apbc", seed=2)
+    h.set_hop_variant(variant)
+    b = sy.gaussian_fermion(d.lat.dims, d.Ls, 611)
+    xs, _ = cg(d.mdagm, b, 1e-12)
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    st = h.solve(bt, x, 1e-9, Hdcg.default_params(algorithm=ALG_CG, outer_prec=F32, maxiter=20000))
+    assert st.status == 0
+    xg = x.cpu().numpy()
+    assert np.sqrt(norm2(b - d.mdagm(xg)) / norm2(b)) <= 1.05e-9
+    assert rel(xg, xs) < 1e-6

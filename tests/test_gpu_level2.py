@@ -249,3 +249,53 @@ def test_three_level_hdcg_meets_the_oracle_solution(coarse_prec):
     assert np.sqrt(norm2(b - d.mdagm(xg)) / norm2(b)) <= 1.05 * tol
     assert rel(xg, xs) <= 1e-6
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# the high-mode preconditioner of Sec. 5.2: Chebyshev polynomial of Q_trunc
+# ---------------------------------------------------------------------------
+
+def test_qtrunc_chebyshev_against_the_oracle(setup):
+    """hdcg_coarse_precondition against the oracle's qtrunc_chebyshev (the
+    truncated stencil, the same interval [lo, hi], order 16): FP32 vectors and
+    15 products with Q_trunc: 1e-5.  The interval the library estimated bounds
+    the spectrum of Q_trunc (numpy's eigenvalues of the oracle's truncation)."""
+    from oracle.solvers import qtrunc_chebyshev, truncate_stencil
+    torch, h, d, g, lat, cb, A1, raw2, phi2, A2, apply_A1 = setup
+    h.set_coarse(A1, prec=F32)
+    lo, hi = h.set_coarse_preconditioner(16)
+    T = stencil_to_dense(truncate_stencil(A1, 1), lat).reshape(lat.Vc * N1, -1)
+    ev = np.linalg.eigvalsh(0.5 * (T + T.conj().T))
+    assert ev[-1] < hi < 1.3 * ev[-1] and lo == pytest.approx(hi / 90)
+    M = qtrunc_chebyshev(A1, lat, 16, lo, hi)
+    R = 3
+    x = sy.complex_normal(3110, (R, lat.Vc, N1))
+    y = torch.zeros((R, lat.Vc, N1, 2), dtype=torch.float64, device="cuda")
+    h.coarse_precondition(to_gpu(x, F64), y, R)
+    want = np.stack([M(x[r]) for r in range(R)])
+    assert rel(from_gpu(y), want) < 1e-5
+    h.set_coarse_preconditioner(0)
+
+
+def test_level1_solve_with_the_qtrunc_smoother(setup):
+    """The level-1 A-DEF2 solve smoothed by M = p(Q_trunc): it meets numpy's
+    dense solution (kappa-bound as above) in no more iterations than with
+    M = 1."""
+    torch, h, d, g, lat, cb, A1, raw2, phi2, A2, apply_A1 = setup
+    R, tol = 2, 1e-7
+    b = sy.complex_normal(3111, (R, lat.Vc, N1))
+    D1 = stencil_to_dense(A1, lat).reshape(lat.Vc * N1, -1)
+    ev = np.linalg.eigvalsh(0.5 * (D1 + D1.conj().T))
+    kappa = ev[-1] / ev[0]
+    xs = np.stack([np.linalg.solve(D1, b[r].ravel()).reshape(lat.Vc, N1) for r in range(R)])
+    h.set_coarse(A1, prec=F32)
+    h.build_subspace(g["block2"], N2, F32, inv_steps=2, inv_tol=1e-5, seed=3112, level=2)
+    h.build_coarse(F32, level=2)
+    x = torch.zeros((R, lat.Vc, N1, 2), dtype=torch.float64, device="cuda")
+    it1 = h.coarse_solve(to_gpu(b, F64), x, R, tol)
+    h.set_coarse_preconditioner(16)
+    x = torch.zeros((R, lat.Vc, N1, 2), dtype=torch.float64, device="cuda")
+    itm = h.coarse_solve(to_gpu(b, F64), x, R, tol)
+    assert rel(from_gpu(x), xs) < kappa * (tol + 5e-7)
+    assert itm <= it1
+    h.set_coarse_preconditioner(0)

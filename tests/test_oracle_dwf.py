@@ -315,3 +315,33 @@ def test_h_stencil_support(golden):
         dc = (lat.coords[lat.sites[1][cb]] - c0 + 5) % 10 - 5
         got.add(tuple(int(v) for v in dc))
     assert got == even
+
+
+@pytest.mark.parametrize("params", [
+    dict(dims=(4, 2, 2, 2), Ls=4, M5=1.8, b=1.0, c=0.0, m=0.01, apbc=False),
+    dict(dims=(2, 2, 4, 2), Ls=4, M5=1.8, b=1.5, c=0.5, m=0.02, apbc=True),
+])
+def test_full_system_source_preparation_and_reconstruction(params):
+    """The full operator's even/odd blocks against the textbook dense 5D matrix,
+    and the Schur-form reduction: with b = prep_source(eta) the solution of
+    H psi_o = b and psi_e = reconstruct(eta_e, psi_o) solve D psi = eta
+    (numpy's dense solve of the textbook matrix)."""
+    p = params
+    U = sy.gauge_field(p["dims"], 0.6, 21)
+    d = DWF(p["dims"], p["Ls"], p["M5"], p["b"], p["c"], p["m"], U, antiperiodic_t=p["apbc"])
+    D, half = _textbook_5d_dense(p["dims"], p["Ls"], p["M5"], p["b"], p["c"], p["m"], U, p["apbc"])
+    shape = d.field_shape
+    psi_e = sy.gaussian_fermion(p["dims"], p["Ls"], 22)
+    psi_o = sy.gaussian_fermion(p["dims"], p["Ls"], 23)
+    eta_e, eta_o = d.apply_full(psi_e, psi_o)
+    want = D @ np.concatenate([psi_e.ravel(), psi_o.ravel()])
+    assert np.abs(np.concatenate([eta_e.ravel(), eta_o.ravel()]) - want).max() < 1e-12 * np.abs(want).max()
+    eta = sy.complex_normal(24, (2 * half,))
+    xs = np.linalg.solve(D, eta)
+    ee, eo = eta[:half].reshape(shape), eta[half:].reshape(shape)
+    b = d.prep_source(ee, eo)
+    Hd = np.stack([d.mdagm(v.reshape(shape)).ravel() for v in np.eye(half)], axis=1)
+    po = np.linalg.solve(Hd, b.ravel()).reshape(shape)
+    pe = d.reconstruct(ee, po)
+    got = np.concatenate([pe.ravel(), po.ravel()])
+    assert np.abs(got - xs).max() < 1e-9 * np.abs(xs).max()
