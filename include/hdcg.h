@@ -134,18 +134,53 @@ typedef struct {
                             2: blocks of the coarse lattice, vectors of the little Dirac
                             operator A (block extents >= 1 dividing the coarse extents,
                             nvec <= 64, prec HDCG_F32); see hdcg_build_coarse */
+    int method;          /* level 1: HDCG_SUBSPACE_INVITER (0) as above, or
+                            HDCG_SUBSPACE_RATIONAL (1): the rational low-pass filter of
+                            Sec. 4.2 (Eq. ratfilt); HDCG_SUBSPACE_CONTINUE (2): inverse
+                            iteration started from the current subspace instead of noise
+                            (the second pass of the two-stage generation, Sec. 4.2) */
+    double filter_lambda;/* RATIONAL: phi = prod_{i < filter_order} (H + lambda + i eps)^-1 eta */
+    double filter_eps;   /*   eps > 0 (any value for order 1) */
+    int filter_order;    /*   1..8 (the paper: 4) */
+    int surface_depth;   /* RATIONAL and CONTINUE: > 0 keeps only the s-slices
+                            s < depth and s >= Ls - depth (SubspaceSurfaceDepth,
+                            Table FineSubspaceParams); 0 keeps all */
 } hdcg_subspace_params;
+
+#define HDCG_SUBSPACE_INVITER 0
+#define HDCG_SUBSPACE_RATIONAL 1
+#define HDCG_SUBSPACE_CONTINUE 2
 
 /* Build the subspace by inverse iteration from Gaussian noise, with block
  * Gram-Schmidt (FP64 arithmetic) after each step (Sec. 2; inverse iteration
  * as named in Sec. 1 and Sec. 5.2.1).  Level 1: vectors of H on the fine
- * lattice, each step a CG on H + inv_shift.  Level 2 (three-level HDCG): the
+ * lattice, each step a CG on H + inv_shift.
+ * Level 1, method HDCG_SUBSPACE_RATIONAL (Sec. 4.2): vector k starts from 4D
+ * Gaussian noise xi_k (the splitmix64 stream seed, canonical order
+ * [k][cb][spin][colour]) placed as P_- xi at s = 0 and P_+ xi at s = Ls - 1,
+ * and is filtered by prod_i (H + lambda + i eps)^-1 = sum_i c_i (H + lambda +
+ * i eps)^-1, c_i = prod_{j != i} 1 / (sigma_j - sigma_i), all shifts from one
+ * multi-shift CG to relative residual inv_tol (cap inv_maxiter), then
+ * truncated to surface_depth and block-orthonormalised.  Method
+ * HDCG_SUBSPACE_CONTINUE applies inv_steps inverse-iteration steps of shift
+ * inv_shift to the current subspace (e.g. one promoted by
+ * hdcg_promote_subspace), then the truncation and block Gram-Schmidt.  Level 2 (three-level HDCG): the
  * same construction on the coarse lattice, Sec. 2 applied to the little Dirac
  * operator; each step solves (A + inv_shift) for up to 16 vectors at once
  * (coarse CG), and the start vectors are the splitmix64 stream seed in
  * canonical order [k][Vc][Nvec].  Level 2 needs the level-1 operator (FP32 or
  * FP16).  Synchronous. */
 int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p);
+
+/* The first pass of the two-stage generation (Sec. 4.2): the level-1 subspace
+ * of src, a handle on the same 4D lattice with fifth extent Ls1 <= Ls (its own
+ * mass; e.g. built with HDCG_SUBSPACE_RATIONAL), promoted into h: the slices
+ * s < ceil(Ls1 / 2) stay at s, the others move to s + Ls - Ls1 (each keeps its
+ * distance to its wall), the bulk between is zero; stored in prec (F64, F32 or
+ * F16) with src's blocking and block-orthonormalised.  Both handles on the
+ * current device; src is not modified.  The second pass is
+ * hdcg_build_subspace with HDCG_SUBSPACE_CONTINUE.  Synchronous. */
+int hdcg_promote_subspace(hdcg_t h, hdcg_t src, int prec);
 
 /* Upload a subspace: level 1: phi canonical complex double [nvec][odd field];
  * level 2: phi canonical complex double [nvec][Vc][Nvec] (stored FP32; prec must
@@ -357,7 +392,10 @@ int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdc
  * prefactor p = fp16(max |real| of the site) (round to nearest even) and 24
  * signed bytes q = clip(rint(127 v / p), -127, 127); decoding gives q p / 127.
  * scale: [nfields][cb][s] IEEE half; q: [nfields][cb][s][24] int8 (the 24
- * reals in canonical order).  FP64 arithmetic.  Asynchronous on the stream. */
+ * reals in canonical order).  FP64 arithmetic.  Asynchronous on the stream.
+ * Range: a site whose largest |real| rounds beyond FP16's 65504 gets an
+ * infinite prefactor and decodes to NaN (the solver's codec input is scaled to
+ * unit RMS first, far inside the range). */
 int hdcg_encode_i8(hdcg_t h, const void* in, void* scale, void* q, int nfields);
 int hdcg_decode_i8(hdcg_t h, const void* scale, const void* q, void* out, int nfields);
 
@@ -383,10 +421,13 @@ int hdcg_get_phase_profile(hdcg_t h, double ms[6]);
  * with register budgets for 1, 2 and 3 resident CTAs per SM; 3 all eight
  * neighbours prefetched (16-bit storage) or double-float arithmetic (FP64
  * storage); 4 and 5 packed FP32 (f32x2) arithmetic with the links staged in
- * shared memory (FP32 and 16-bit storage).  By default (variant -1) the first
- * launch of each pass times the variants and keeps the fastest; 0..5 forces
- * one (for FP64 storage variants 4 and 5 fall back to 0).  HDCG_ERR_ARG
- * outside -1..5. */
+ * shared memory (FP32 and 16-bit storage; measured slower than 0-3, and
+ * rounding differently, so only run when forced).  By default (variant -1)
+ * the first launch of each pass times variants 0-3 and keeps the fastest
+ * (0-2 and the 16-bit variant 3 give identical bits; for FP64 storage
+ * variant 3's double-float arithmetic agrees with FP64 to about 1e-14); 0..5
+ * forces one (for FP64 storage variants 4 and 5 fall back to 0).
+ * HDCG_ERR_ARG outside -1..5. */
 int hdcg_set_hop_variant(hdcg_t h, int variant);
 
 /* Count of library kernel launches issued on the handle since creation. */

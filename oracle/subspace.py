@@ -29,8 +29,10 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``): never imported by the library.
                wall, the bulk between is zero (our reading of the promotion to
                the full system's surfaces in Sec. 4.2).
 * ``two_pass_subspace``  the two-stage generation (Sec. 4.2, Table optimised,
-               first and second pass controls): the filter on a reduced-Ls
-               operator with its own mass, promotion, then one shifted inversion
+               first and second pass controls): the subspace of a reduced-Ls
+               operator with its own mass (the filter and block Gram-Schmidt:
+               the first pass yields a subspace), promotion (an isometry, so the
+               promoted vectors stay block-orthonormal), then one shifted inversion
                (H + lam2)^-1 of every promoted vector on the full system by
                A-DEF2 deflated with the promoted vectors (the solver that the
                first pass provides), to a loose residual, and block Gram-Schmidt.
@@ -210,8 +212,7 @@ def two_pass_subspace(d: DWF, blocking: Blocking, nvec: int, seed: int, Ls1: int
     (depth > 0) and block Gram-Schmidt."""
     from .solvers import DeflationSpace, adef2
     d1 = DWF(d.lat.dims, Ls1, d.M5, d.b, d.c, mass1, d.U, antiperiodic_t=d.apbc)
-    eta = wall_noise(d.lat.V // 2, Ls1, nvec, seed)
-    phi1 = np.stack([rational_filter(d1.mdagm, e, lam, eps, tol1) for e in eta])
+    phi1 = rational_subspace(d1.mdagm, Blocking(d1, blocking.block), nvec, seed, lam, eps, tol=tol1)
     v = promote(phi1, d.Ls)
     if lam2 > 0:
         def Hs(x):

@@ -15,6 +15,7 @@ import numpy as np
 F64, F32, F16, BF16, BF16T, DF64 = 0, 1, 2, 3, 4, 5
 PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "bf16t": BF16T}
 ALG_CG, ALG_ADEF2 = 0, 1
+SUBSPACE_INVITER, SUBSPACE_RATIONAL, SUBSPACE_CONTINUE = 0, 1, 2
 _ERRORS = {1: "not converged", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
            -4: "non-finite value", -5: "Krylov breakdown", -6: "device wait timed out", -7: "missing prerequisite"}
 
@@ -35,7 +36,9 @@ class HdcgError(RuntimeError):
 class SubspaceParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inv_steps", ctypes.c_int), ("inv_shift", ctypes.c_double), ("inv_tol", ctypes.c_double),
-                ("inv_maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("level", ctypes.c_int)]
+                ("inv_maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("level", ctypes.c_int),
+                ("method", ctypes.c_int), ("filter_lambda", ctypes.c_double), ("filter_eps", ctypes.c_double),
+                ("filter_order", ctypes.c_int), ("surface_depth", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -74,6 +77,7 @@ _SIGS = {
     "hdcg_reconstruct": (_I, [_P, _P, _P, _P, _I]),
     "hdcg_build_subspace": (_I, [_P, ctypes.POINTER(SubspaceParams)]),
     "hdcg_set_subspace": (_I, [_P, _I, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
+    "hdcg_promote_subspace": (_I, [_P, _P, _I]),
     "hdcg_get_subspace": (_I, [_P, _I, _P]),
     "hdcg_build_coarse": (_I, [_P, _I, _I]),
     "hdcg_get_coarse": (_I, [_P, _I, _P]),
@@ -213,10 +217,16 @@ class Hdcg:
 
     # -- subspace and coarse operator -----------------------------------------
     def build_subspace(self, block, nvec, prec=F32, inv_steps=3, inv_shift=0.0, inv_tol=1e-4,
-                       inv_maxiter=20000, seed=0, level=1):
+                       inv_maxiter=20000, seed=0, level=1, method=SUBSPACE_INVITER, filter_lambda=0.0,
+                       filter_eps=0.0, filter_order=4, surface_depth=0):
         p = SubspaceParams((ctypes.c_int * 4)(*block), nvec, prec, inv_steps, inv_shift, inv_tol,
-                           inv_maxiter, seed, int(level))
+                           inv_maxiter, seed, int(level), int(method), float(filter_lambda), float(filter_eps),
+                           int(filter_order), int(surface_depth))
         return self._check(self._L.hdcg_build_subspace(self.h, ctypes.byref(p)))
+
+    def promote_subspace(self, src, prec=F32):
+        """This handle's subspace := src's (fifth extent Ls1 <= Ls) promoted to Ls."""
+        return self._check(self._L.hdcg_promote_subspace(self.h, src.h, int(prec)))
 
     def set_subspace(self, block, phi, prec=F32, already_orthonormal=False, level=1):
         nvec = int(phi.shape[0])

@@ -414,6 +414,43 @@ void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, cons
   ++c.launches;
 }
 
+// amax[r] = max |real| of field r (as float bits: non-negative floats order like
+// their bit patterns)
+template <typename S>
+__global__ void k_amax(const uint4* __restrict__ x, size_t n5, size_t fs, unsigned* amax) {
+  using R = typename Store<S>::real;
+  const int rr = blockIdx.y;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float m = 0.f;
+  if (t < n5) {
+    R v[24];
+    load_spinor<S, R>(x + rr * fs, t, n5, v);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) m = fmaxf(m, fabsf((float)v[i]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(amax + rr, __float_as_uint(m));
+}
+
+__global__ void k_cap_den(const unsigned* amax, const double* num, double* den, double peak, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  const double m = (double)__uint_as_float(amax[r]) / peak;
+  const double d = num[0] * m * m;
+  if (d > den[r]) den[r] = d;
+}
+
+void cap_scale(Ctx& c, const uint4* x, int prec, const double* num, double* den, double peak, unsigned* amax,
+               int nrhs) {
+  HDCG_CUDA(cudaMemsetAsync(amax, 0, nrhs * sizeof(unsigned), c.stream));
+  const size_t fs = c.field_bytes(prec) / 16;
+  DISPATCH_PREC(prec, S, { k_amax<S><<<dim3(blocks_for(c.n5), nrhs), 256, 0, c.stream>>>(x, c.n5, fs, amax); });
+  k_cap_den<<<1, 32, 0, c.stream>>>(amax, num, den, peak, nrhs);
+  HDCG_CUDA(cudaGetLastError());
+  c.launches += 2;
+}
+
 void update_xr(Ctx& c, int prec_x, uint4* x, int prec, const uint4* p, uint4* r, const uint4* w,
                ScalarRef alpha, int sign_x, double* rr_out) {
   const unsigned g = blocks_for(c.n5);

@@ -65,6 +65,11 @@ void axpby(Ctx& c, double a, int prec_x, const uint4* x, double b, int prec_y, u
 // (den is read per right-hand side: den[r]; num[0] is shared)
 void convert_scaled(Ctx& c, const uint4* in, int pin, uint4* out, int pout, const double* num, const double* den,
                     int inv, int nrhs = 1);
+// den[r] = max(den[r], num[0] (amax_r / peak)^2), amax_r the largest |real| of
+// field r of x: the scale sqrt(num / den) then also keeps every real of the
+// scaled field within peak (amax: device scratch of nrhs unsigned)
+void cap_scale(Ctx& c, const uint4* x, int prec, const double* num, double* den, double peak, unsigned* amax,
+               int nrhs = 1);
 // y = sqrt(num/den)^(inv ? -1 : 1) x
 void scale_dev(Ctx& c, int prec, const uint4* x, uint4* y, const double* num, const double* den, int inv);
 

@@ -12,6 +12,9 @@ namespace hdcg {
 int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_params& prm, hdcg_stats* st,
           bool on_device);
 void build_subspace(Ctx& c, const hdcg_subspace_params& p);
+void build_subspace_rational(Ctx& c, const hdcg_subspace_params& p);
+void continue_subspace(Ctx& c, const hdcg_subspace_params& p);
+void promote_subspace(Ctx& c, Ctx& src, int prec);
 void build_coarse(Ctx& c, int prec);
 void prep_source(Ctx& c, const void* eta_e, const void* eta_o, void* b);
 void reconstruct(Ctx& c, const void* eta_e, const void* psi_o, void* psi_e);
@@ -253,11 +256,25 @@ int hdcg_build_subspace(hdcg_t h, const hdcg_subspace_params* p) {
     const int level = p->level == 0 ? 1 : p->level;
     check_level(level);
     if (level == 1) {
-      build_subspace(c, *p);
+      if (p->method == HDCG_SUBSPACE_RATIONAL) build_subspace_rational(c, *p);
+      else if (p->method == HDCG_SUBSPACE_CONTINUE) continue_subspace(c, *p);
+      else {
+        HDCG_REQUIRE(p->method == HDCG_SUBSPACE_INVITER, HDCG_ERR_ARG, "unknown subspace method");
+        build_subspace(c, *p);
+      }
     } else {
+      HDCG_REQUIRE(p->method == HDCG_SUBSPACE_INVITER, HDCG_ERR_ARG, "level 2 builds by inverse iteration");
       HDCG_REQUIRE(c.sub && c.coarse, HDCG_ERR_STATE, "a level-2 subspace needs the level-1 operator");
       level2_build_subspace(c, *c.coarse, *c.sub, *p);
     }
+  });
+  return HDCG_OK;
+}
+
+int hdcg_promote_subspace(hdcg_t h, hdcg_t src, int prec) {
+  HDCG_ENTRY(h, {
+    HDCG_REQUIRE(src != nullptr, HDCG_ERR_ARG, "src handle is NULL");
+    promote_subspace(c, *reinterpret_cast<Ctx*>(src), prec);
   });
   return HDCG_OK;
 }

@@ -159,6 +159,8 @@ void subspace_init(Ctx& c, Subspace& s, const int block[4], int nvec, int prec);
 // Gaussian noise in every subspace vector (splitmix64 counter stream, Box-Muller),
 // drawn in canonical order [k][cb][s][spin][colour][re, im]
 void subspace_noise(Ctx& c, Subspace& s, uint64_t seed);
+// v <- (H + shift)^-1 v by CG in precision wp, v stored in vprec (solver.cu)
+void inverse_step(Ctx& c, int wp, uint4* v, int vprec, double shift, double tol, int maxiter);
 // block orthonormalisation: two rounds of (block Gram matrix in FP64,
 // Cholesky G = R^dag R in FP64, Phi <- Phi R^-1)
 void block_orthonormalise(Ctx& c, Subspace& s);

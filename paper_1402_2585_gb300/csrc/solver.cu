@@ -35,8 +35,15 @@ enum {
 enum {
   D_PW = 0, D_RR = 1, D_RY = 2, D_RYN = 3 /* 2 */, D_BB = 6, D_TMP = 7, D_NREAL = 8,
   D_MRR = 16 /* 2 */, D_MPW = 18, D_MPP = 19, D_CRR = 24 /* 2 */, D_CPW = 26, D_CPP = 27,
-  D_RYO = 30 /* 2 */
+  D_RYO = 30 /* 2 */, D_AMAX = 32 /* unsigned */
 };
+
+// 16-bit preconditioner input: unit RMS per real, unless that puts a real
+// beyond SCALED_PEAK (a localised residual, e.g. of a point source, whose
+// peak is up to sqrt(#reals) times its RMS): then the peak is SCALED_PEAK.
+// The sloppy H multiplies magnitudes by up to ~10^2, so FP16's 65504 is not
+// reached, and reals down to 1e-6 of the peak stay normal FP16 numbers.
+constexpr double SCALED_PEAK = 64.0;
 
 static double* dsc(Ctx& c, int slot) { return c.scalars.as<double>() + slot * RMAX; }
 
@@ -149,6 +156,7 @@ static void apply_M1(Ctx& c, int op, int sp, const uint4* r, uint4* y, const hdc
   const bool scaled = is_16bit(sp);
   if (scaled) {
     norm2(c, r, op, 0, dsc(c, D_TMP));
+    cap_scale(c, r, op, dsc(c, D_NREAL), dsc(c, D_TMP), SCALED_PEAK, reinterpret_cast<unsigned*>(dsc(c, D_AMAX)));
     uint4* t = c.scratch(sp, SL_RS);
     convert_scaled(c, r, op, t, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0);
     rs = t;
@@ -194,6 +202,8 @@ static void start_vector(Ctx& c, int sp, const uint4* b64, uint4* xhi, const hdc
   const bool scaled = is_16bit(sp);
   if (scaled) {
     norm2(c, b64, HDCG_F64, 0, dsc(c, D_TMP));
+    cap_scale(c, b64, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), SCALED_PEAK,
+              reinterpret_cast<unsigned*>(dsc(c, D_AMAX)));
     convert_scaled(c, b64, HDCG_F64, bs, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0);
   } else {
     convert_field(c, b64, HDCG_F64, bs, sp);
@@ -380,6 +390,8 @@ static void apply_M1_multi(Ctx& c, int op, int sp, int R, const uint4* r, uint4*
   const bool scaled = is_16bit(sp);
   if (scaled) {
     norm2(c, r, op, 0, dsc(c, D_TMP), R);
+    cap_scale(c, r, op, dsc(c, D_NREAL), dsc(c, D_TMP), SCALED_PEAK, reinterpret_cast<unsigned*>(dsc(c, D_AMAX)),
+              R);
     uint4* t = c.scratch(sp, SL_RS, R);
     convert_scaled(c, r, op, t, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0, R);
     rs = t;
@@ -428,6 +440,8 @@ static void start_vector_multi(Ctx& c, int sp, int R, const uint4* b64, uint4* x
   const bool scaled = is_16bit(sp);
   if (scaled) {
     norm2(c, b64, HDCG_F64, 0, dsc(c, D_TMP), R);
+    cap_scale(c, b64, HDCG_F64, dsc(c, D_NREAL), dsc(c, D_TMP), SCALED_PEAK,
+              reinterpret_cast<unsigned*>(dsc(c, D_AMAX)), R);
     convert_scaled(c, b64, HDCG_F64, bs, sp, dsc(c, D_NREAL), dsc(c, D_TMP), 0, R);
     // x_hi = unscale(Q b_s), prolonged straight into FP64
     apply_Q_multi(c, sp, R, bs, xhi, HDCG_F64, nullptr, prm, st, -1, dsc(c, D_NREAL), dsc(c, D_TMP));
@@ -662,6 +676,15 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
 // ---------------------------------------------------------------------------
 // subspace by inverse iteration and the coarse operator
 // ---------------------------------------------------------------------------
+// v <- (H + shift)^-1 v by CG in precision wp (v stored in vprec)
+void inverse_step(Ctx& c, int wp, uint4* v, int vprec, double shift, double tol, int maxiter) {
+  uint4* bk = c.scratch(wp, SL_CGB);
+  uint4* xk = c.scratch(wp, SL_CGX);
+  convert_field(c, v, vprec, bk, wp);
+  cg_shifted(c, wp, bk, xk, shift, 0, tol, maxiter, nullptr);
+  convert_field(c, xk, wp, v, vprec);
+}
+
 void build_subspace(Ctx& c, const hdcg_subspace_params& p) {
   HDCG_REQUIRE(c.have_gauge && c.have_dwf, HDCG_ERR_STATE, "gauge field and DWF parameters required");
   for (int mu = 0; mu < 4; ++mu)
@@ -675,14 +698,8 @@ void build_subspace(Ctx& c, const hdcg_subspace_params& p) {
   subspace_init(c, s, p.block, p.nvec, round_at_end ? HDCG_F32 : p.prec);
   subspace_noise(c, s, p.seed);
   const int wp = p.prec == HDCG_F64 ? HDCG_F64 : HDCG_F32;
-  uint4* bk = c.scratch(wp, SL_CGB);
-  uint4* xk = c.scratch(wp, SL_CGX);
   for (int step = 0; step < p.inv_steps; ++step) {
-    for (int k = 0; k < s.nvec; ++k) {
-      convert_field(c, s.vec(c, k), s.prec, bk, wp);
-      cg_shifted(c, wp, bk, xk, p.inv_shift, 0, p.inv_tol, p.inv_maxiter, nullptr);
-      convert_field(c, xk, wp, s.vec(c, k), s.prec);
-    }
+    for (int k = 0; k < s.nvec; ++k) inverse_step(c, wp, s.vec(c, k), s.prec, p.inv_shift, p.inv_tol, p.inv_maxiter);
     block_orthonormalise(c, s);
   }
   if (p.inv_steps <= 0) block_orthonormalise(c, s);

@@ -18,7 +18,8 @@ def test_header_declares_the_boundary():
               "hdcg_build_subspace", "hdcg_set_subspace", "hdcg_build_coarse", "hdcg_get_coarse",
               "hdcg_restrict", "hdcg_prolong", "hdcg_coarse_apply", "hdcg_solve", "hdcg_last_error",
               "hdcg_destroy", "hdcg_prep_source", "hdcg_reconstruct", "hdcg_restrict_coarse",
-              "hdcg_prolong_coarse"]:
+              "hdcg_prolong_coarse", "hdcg_promote_subspace", "hdcg_coarse_precondition",
+              "hdcg_set_coarse_preconditioner", "hdcg_encode_i8", "hdcg_decode_i8"]:
         assert n in names
 
 

@@ -25,7 +25,7 @@ from oracle.dwf import DWF, norm2
 from oracle.level2 import CoarseBlocking
 from oracle.solvers import cg
 from paper_1402_2585_gb300 import ALG_ADEF2, F16, F32, F64, Hdcg
-from tests.gpu_util import from_gpu, rel, to_gpu, torch_or_skip
+from tests.gpu_util import from_gpu, rel, to_gpu, torch_or_skip, cg_kappa
 
 pytestmark = pytest.mark.gpu
 
@@ -186,39 +186,10 @@ def _oracle_solution(d, b):
     """The oracle's CG solution (to 1e-13) and kappa, computed once per module."""
     key = (d.lat.dims, d.Ls)
     if key not in _SOLUTIONS:
-        _SOLUTIONS[key] = _cg_kappa(d.mdagm, b, 1e-13)
+        _SOLUTIONS[key] = cg_kappa(d.mdagm, b, 1e-13)
     return _SOLUTIONS[key]
 
 
-def _cg_kappa(apply_H, b, tol):
-    """CG on H from zero with the Lanczos tridiagonal of its coefficients
-    (diagonal 1/alpha_k + beta_{k-1}/alpha_{k-1}, off-diagonal sqrt(beta_k)/alpha_k):
-    returns (x, kappa) with kappa the ratio of the extreme Ritz values, which
-    have converged to H's extreme eigenvalues once CG reaches tol ~ 1e-13."""
-    x = np.zeros_like(b)
-    r = b.copy()
-    p = r.copy()
-    rr = norm2(r)
-    bb = rr
-    al, be = [], []
-    while np.sqrt(rr / bb) > tol and len(al) < 20000:
-        w = apply_H(p)
-        a = rr / np.vdot(p, w).real
-        x += a * p
-        r -= a * w
-        rn = norm2(r)
-        al.append(a)
-        be.append(rn / rr)
-        p = r + (rn / rr) * p
-        rr = rn
-    k = len(al)
-    T = np.zeros((k, k))
-    for i in range(k):
-        T[i, i] = 1.0 / al[i] + (be[i - 1] / al[i - 1] if i else 0.0)
-        if i + 1 < k:
-            T[i, i + 1] = T[i + 1, i] = np.sqrt(be[i]) / al[i]
-    ev = np.linalg.eigvalsh(T)
-    return x, ev[-1] / ev[0]
 
 
 @pytest.mark.parametrize("coarse_prec", [F32, F16])

@@ -157,3 +157,63 @@ def test_inverse_iteration_enriches_low_modes():
     rq_phi = [inner(v, d.mdagm(v)).real / norm2(v) for v in phi]
     rq_noise = [inner(v, d.mdagm(v)).real / norm2(v) for v in noise]
     assert max(rq_phi) < 0.05 * min(rq_noise)
+
+
+def _dense_H(d):
+    """H as a dense matrix, one oracle apply per unit vector."""
+    shape = d.field_shape
+    n = int(np.prod(shape))
+    Hm = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        Hm[:, j] = d.mdagm(e.reshape(shape)).ravel()
+        e[j] = 0.0
+    return Hm
+
+
+def _block_qr(V, bl, shape):
+    """Per block, the Q factor of numpy's QR of the block pieces with the
+    diagonal of R made real positive (the unique such factorisation)."""
+    out = np.zeros_like(V)
+    W = V.reshape((V.shape[0],) + shape)
+    O = out.reshape((V.shape[0],) + shape)
+    for sites in bl.sites_of_block:
+        X = W[:, sites].reshape(V.shape[0], -1).T
+        Q, R = np.linalg.qr(X)
+        ph = np.diag(R) / np.abs(np.diag(R))
+        O[:, sites] = (Q * ph).T.reshape((V.shape[0], len(sites)) + shape[1:])
+    return out
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.3])
+def test_inverse_iteration_subspace_is_dense_inverse_iteration(shift):
+    """Pin: two steps of phi <- blockQR((H + shift)^-1 phi) with H assembled
+    densely, numpy's linear solve and numpy's QR per block (4x4x2x2 lattice,
+    Ls 2, 2^4 blocks).  A dropped shift or sign, a skipped orthonormalisation or
+    a wrong block assignment all fail."""
+    dims, Ls = (4, 4, 2, 2), 2
+    d = DWF(dims, Ls, 1.8, 1.5, 0.5, 0.1, sy.gauge_field(dims, 0.4, 330))
+    bl = Blocking(d, (2, 2, 2, 2))
+    noise = sy.gaussian_fermions(dims, Ls, 331, 3)
+    Hm = _dense_H(d) + shift * np.eye(int(np.prod(d.field_shape)))
+    V = noise.reshape(3, -1)
+    for _ in range(2):
+        V = np.linalg.solve(Hm, V.T).T
+        V = _block_qr(V, bl, d.field_shape)
+    got = inverse_iteration_subspace(d.mdagm, noise, bl, steps=2, shift=shift, tol=1e-14)
+    assert np.abs(got.reshape(3, -1) - V).max() < 1e-9
+    if shift:
+        other = inverse_iteration_subspace(d.mdagm, noise, bl, steps=2, shift=-shift / 2, tol=1e-14)
+        assert np.abs(other.reshape(3, -1) - V).max() > 1e-3
+
+
+def test_cg_kappa_on_a_diagonal_operator():
+    """The Lanczos tridiagonal of CG's coefficients recovers lambda_max /
+    lambda_min of a diagonal operator with known spectrum."""
+    from tests.gpu_util import cg_kappa
+    lam = np.linspace(0.01, 5.0, 400)
+    b = sy.complex_normal(332, (400,))
+    x, k = cg_kappa(lambda v: lam * v, b, 1e-13)
+    assert abs(k - 500.0) < 1e-6 * 500
+    assert np.abs(x - b / lam).max() < 1e-9

@@ -174,3 +174,15 @@ def test_second_pass_coarse_operator_is_shifted_by_lam2():
     As = coarse_dense_bruteforce(lambda v: d.mdagm(v) + lam2 * v, basis, bl)
     eye = np.einsum("ab,jk->ajbk", np.eye(bl.Vc), np.eye(3))
     assert np.abs(As - (A + lam2 * eye)).max() < 1e-12 * np.abs(A).max()
+
+
+def test_promotion_keeps_block_orthonormality():
+    """Promotion moves whole s-slices without dropping any, so a block-orthonormal
+    Ls1 subspace stays block-orthonormal in Ls (Gram-Schmidt leaves it unchanged)."""
+    from oracle.coarse import block_gram_schmidt
+    dims = (8, 4, 4, 4)
+    d1 = DWF(dims, 4, 1.8, 1.5, 0.5, 0.05, sy.gauge_field(dims, 0.4, 1719))
+    d = DWF(dims, 8, 1.8, 1.5, 0.5, 0.01, d1.U)
+    phi1 = block_gram_schmidt(sy.gaussian_fermions(dims, 4, 1720, 3), Blocking(d1, (4, 4, 4, 4)))
+    v = promote(phi1, 8)
+    assert np.abs(block_gram_schmidt(v, Blocking(d, (4, 4, 4, 4))) - v).max() < 1e-13
