@@ -75,6 +75,32 @@ extern "C" {
 /* solver algorithms */
 #define HDCG_ALG_CG    0  /* plain CG on H (the red-black normal-equation baseline) */
 #define HDCG_ALG_ADEF2 1  /* A-DEF2: V_start = Qb + P_R x, M1 = P_R M_IRS + Q (Table algos) */
+/* The rest of Table algos (Sec. 4.5, Fig. pcg_general), with Q = P A^-1 R,
+ * P_L = 1 - H Q, P_R = 1 - Q H and the smoother M of hdcg_params.smoother.
+ * These run the generalised PCG one right-hand side at a time with every
+ * field and operator in outer_prec (F64 or F32; sloppy_prec, batch and
+ * reliable_delta are not used), stop on the recursive residual, and report
+ * the FP64 true residual. */
+#define HDCG_ALG_PREC   2   /* M1 = M */
+#define HDCG_ALG_AD     3   /* M1 = M + Q */
+#define HDCG_ALG_DEF1   4   /* M1 = M, M3 = P_L (start residual projected), V_end = Q b + P_R x */
+#define HDCG_ALG_DEF2   5   /* M1 = M, M2 = P_R, V_start = Q b + P_R x */
+#define HDCG_ALG_ADEF1  6   /* M1 = M P_L + Q (M2 = 1) */
+#define HDCG_ALG_BNN    7   /* M1 = P_R M P_L + Q */
+#define HDCG_ALG_BNN_DEF2START 8   /* BNN from V_start = Q b + P_R x */
+#define HDCG_ALG_V11    9   /* M1 = M P_L + P_R M + Q - M P_L H M (symmetric two-grid cycle) */
+#define HDCG_ALG_MSSDEF 10  /* A-DEF2 with M = 1 (the little Dirac operator alone) */
+#define HDCG_ALG_ADEF2_FAMILY 11  /* A-DEF2 in the generalised PCG (same algorithm as
+                                     HDCG_ALG_ADEF2 without its mixed precision) */
+
+/* smoothers of the family solves (Table preconditioner) */
+#define HDCG_SMOOTHER_MIRS      0  /* mirs_iter CG iterations on H + mirs_shift from zero */
+#define HDCG_SMOOTHER_MIRSPOLY  1  /* the same CG's alpha_k, beta_k frozen from one pass on
+                                      the right-hand side b and replayed: a fixed polynomial
+                                      in H, linear and Hermitian */
+#define HDCG_SMOOTHER_CHEBYSHEV 2  /* p(H), 1 - x p(x) = T_n((theta - x)/delta) / T_n(theta/delta)
+                                      on [cheb_lo, cheb_hi], n = cheb_order */
+#define HDCG_SMOOTHER_NONE      3  /* M = 1 */
 
 typedef struct hdcg_ctx* hdcg_t;
 
@@ -360,6 +386,9 @@ typedef struct {
                               the precision of the paper's compressed preconditioner
                               communication: 0 none, 1 each FP32 word truncated to 16 bits,
                               2 8-bit integers with an FP16 prefactor per 5D site */
+    int smoother;          /* family solves (algorithm >= 2): HDCG_SMOOTHER_* */
+    int cheb_order;        /* HDCG_SMOOTHER_CHEBYSHEV: order n (>= 1) and interval */
+    double cheb_lo, cheb_hi;
 } hdcg_params;
 
 typedef struct {

@@ -15,6 +15,14 @@ import numpy as np
 F64, F32, F16, BF16, BF16T, DF64 = 0, 1, 2, 3, 4, 5
 PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "bf16t": BF16T}
 ALG_CG, ALG_ADEF2 = 0, 1
+ALG_PREC, ALG_AD, ALG_DEF1, ALG_DEF2, ALG_ADEF1, ALG_BNN, ALG_BNN_DEF2START, ALG_V11, ALG_MSSDEF, ALG_ADEF2_FAMILY = \
+    range(2, 12)
+FAMILY = {"PREC": ALG_PREC, "AD": ALG_AD, "DEF1": ALG_DEF1, "DEF2": ALG_DEF2, "A-DEF1": ALG_ADEF1,
+          "A-DEF2": ALG_ADEF2_FAMILY, "BNN": ALG_BNN, "BNN-DEF2-start": ALG_BNN_DEF2START, "V11": ALG_V11,
+          "MssDef": ALG_MSSDEF}
+ALG_NAMES = {"CG": ALG_CG, "A-DEF2": ALG_ADEF2, "A-DEF2 (generalised PCG)": ALG_ADEF2_FAMILY,
+             **{k: v for k, v in FAMILY.items() if k != "A-DEF2"}}
+SMOOTHER_MIRS, SMOOTHER_MIRSPOLY, SMOOTHER_CHEBYSHEV, SMOOTHER_NONE = 0, 1, 2, 3
 SUBSPACE_INVITER, SUBSPACE_RATIONAL, SUBSPACE_CONTINUE = 0, 1, 2
 _ERRORS = {1: "not converged", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
            -4: "non-finite value", -5: "Krylov breakdown", -6: "device wait timed out", -7: "missing prerequisite"}
@@ -45,7 +53,9 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int), ("outer_prec", ctypes.c_int), ("sloppy_prec", ctypes.c_int),
                 ("mirs_iter", ctypes.c_int), ("mirs_shift", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxiter", ctypes.c_int), ("flexible", ctypes.c_int), ("maxiter", ctypes.c_int),
-                ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int), ("sloppy_codec", ctypes.c_int)]
+                ("reliable_delta", ctypes.c_double), ("batch", ctypes.c_int), ("sloppy_codec", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("cheb_order", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double)]
 
 
 class LdopParams(ctypes.Structure):

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhdcg.so")
 SOURCES = ["dwf.cu", "dwf_f64.cu", "dwf_f32.cu", "dwf_f16.cu", "dwf_bf16.cu", "dwf_bf16t.cu", "dwf_df.cu", "blas.cu",
-           "coarse.cu", "coarse_tc.cu", "ldop.cu", "level2.cu", "schur.cu", "qtrunc.cu", "codec.cu", "subspace.cu", "solver.cu", "capi.cu"]
+           "coarse.cu", "coarse_tc.cu", "ldop.cu", "level2.cu", "schur.cu", "qtrunc.cu", "codec.cu", "subspace.cu", "family.cu", "solver.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

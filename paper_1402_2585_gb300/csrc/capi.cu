@@ -540,6 +540,10 @@ void hdcg_default_params(hdcg_params* p) {
   p->reliable_delta = 0.01;
   p->batch = 1;
   p->sloppy_codec = 0;
+  p->smoother = HDCG_SMOOTHER_MIRS;
+  p->cheb_order = 16;
+  p->cheb_lo = 0.5;
+  p->cheb_hi = 45.0;
 }
 
 int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdcg_params* p, hdcg_stats* st,
@@ -550,7 +554,8 @@ int hdcg_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, const hdc
     hdcg_params prm;
     if (p) prm = *p;
     else hdcg_default_params(&prm);
-    HDCG_REQUIRE(prm.algorithm == HDCG_ALG_CG || prm.algorithm == HDCG_ALG_ADEF2, HDCG_ERR_ARG, "unknown algorithm");
+    HDCG_REQUIRE(prm.algorithm >= HDCG_ALG_CG && prm.algorithm <= HDCG_ALG_ADEF2_FAMILY, HDCG_ERR_ARG,
+                 "unknown algorithm");
     HDCG_REQUIRE(prm.maxiter > 0 && prm.reliable_delta > 0 && prm.reliable_delta < 1, HDCG_ERR_ARG,
                  "bad iteration parameters");
     HDCG_REQUIRE(prm.mirs_iter >= 1 && prm.coarse_tol > 0 && prm.coarse_maxiter > 0, HDCG_ERR_ARG,

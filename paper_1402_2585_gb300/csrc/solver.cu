@@ -625,6 +625,9 @@ static int batch_size(Ctx& c, const hdcg_params& prm, int nrhs, bool on_device) 
   return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)RMAX, (size_t)nrhs), fit));
 }
 
+bool is_family_algorithm(int alg);
+int solve_family(Ctx& c, const uint4* b64, uint4* x64, double tol, const hdcg_params& prm, hdcg_stats* st);
+
 int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_params& prm, hdcg_stats* st,
           bool on_device) {
   HDCG_REQUIRE(nrhs >= 1, HDCG_ERR_ARG, "nrhs >= 1");
@@ -638,7 +641,8 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
     const double nreal = (double)c.n5 * 24.0;
     HDCG_CUDA(cudaMemcpyAsync(dsc(c, D_NREAL), &nreal, sizeof(double), cudaMemcpyHostToDevice, c.stream));
   }
-  const int chunk = batch_size(c, prm, nrhs, on_device);
+  const bool family = is_family_algorithm(prm.algorithm);
+  const int chunk = family ? 1 : batch_size(c, prm, nrhs, on_device);
   st->batch_rhs = chunk;
   for (int k0 = 0; k0 < nrhs; k0 += chunk) {
     const int R = std::min(chunk, nrhs - k0);
@@ -656,7 +660,8 @@ int solve(Ctx& c, const void* b, void* x, int nrhs, double tol, const hdcg_param
     int rc;
     {
       PhaseTimer pt(c, PH_TOTAL);
-      rc = R == 1 ? solve_one(c, b64, x64, tol, prm, st) : solve_batch(c, b64, x64, R, tol, prm, st);
+      rc = family ? solve_family(c, b64, x64, tol, prm, st)
+           : R == 1 ? solve_one(c, b64, x64, tol, prm, st) : solve_batch(c, b64, x64, R, tol, prm, st);
     }
     if (rc != HDCG_OK) worst = rc;
     if (on_device) {

@@ -28,7 +28,7 @@ def _header_macros(prefix):
 def _binding_codes():
     codes = {"HDCG_" + n: getattr(bd, n) for n in ("F64", "F32", "F16", "BF16", "BF16T", "DF64")}
     for n in dir(bd):
-        if re.fullmatch(r"ALG_[A-Z0-9_]+", n) and n != "ALG_NAMES":
+        if re.fullmatch(r"(ALG|SMOOTHER|SUBSPACE)_[A-Z0-9_]+", n) and n != "ALG_NAMES":
             codes["HDCG_" + n] = getattr(bd, n)
     return codes
 
