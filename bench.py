@@ -389,6 +389,7 @@ def run_ours(args, w):
                               "op_bytes": op_p, "GBps": by_p / (ms_p / 1e3) / 1e9 if ms_p > 0 else None}
     phases = h.get_phase_profile()
     h.set_profiling(False)
+    coarse_rl = coarse_roofline(h, w, args)
 
     # the solution's true residual, recomputed by the library's FP64-accurate operator
     true_res = s0["true_residual"]
@@ -509,6 +510,7 @@ def run_ours(args, w):
                  "h_applies_per_rhs": n_h / nrhs,
                  "h_applies_per_rhs_reference_arm": H_APPLIES_PER_RHS.get(w.name)},
         "phases_ms_per_solve_profiled": phases,
+        "coarse_roofline": coarse_rl,
         "hop_profile": hop_all,
         "batched": batched,
         "setup_seconds": setup,
@@ -518,6 +520,32 @@ def run_ours(args, w):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def coarse_roofline(h, w, args):
+    """The level-1 little Dirac stencil (Sec. 5.1) on its own: the tensor-core
+    apply (k_capply_tc) of the workload's coarse operator to 1 and to 12
+    coarse vectors, timed by the library with CUDA events over 20 launches
+    after 3 warm-ups (hdcg_time_coarse_apply).
+    Algorithmic bytes per apply: the stored operator, 81 Nvec^2 complex per
+    coarse site (FP16: 4 B per complex; FP32 as FP16 hi + lo: 8 B), read once
+    for all right-hand sides; the vectors (16 B per complex in and out of the
+    coarse layout) are a few percent on top and not counted."""
+    cp = args.coarse_prec or w.coarse_prec or w.prec
+    bpc = {"f16": 4, "f32": 8, "f64": 16}.get(cp)
+    vc = int(np.prod([d // b for d, b in zip(w.dims, w.block)]))
+    peak, peak_kind = peaks()
+    out = {"kernel": "k_capply_tc (tcgen05)" if cp in ("f16", "f32") else "capply (CUDA cores)",
+           "storage": cp, "coarse_sites": vc, "nvec": w.nvec, "peak": peak, "peak_kind": f"{peak_kind} HBM copy"}
+    if cp not in ("f16", "f32"):
+        return out
+    for R in (1, 12):
+        t = h.time_coarse_apply(R, 20) / 1e6
+        bytes_ = vc * 81 * w.nvec ** 2 * bpc
+        out[f"rhs{R}"] = {"us_per_apply": t * 1e6, "operator_bytes": bytes_,
+                          "GBps": bytes_ / t / 1e9, "frac": bytes_ / t / 1e9 / peak,
+                          "tflops": 8.0 * vc * 81 * w.nvec ** 2 * R / t / 1e12}
+    return out
 
 
 def roofline(w, hop_all, pname, peak, peak_kind, nrhs):

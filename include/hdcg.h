@@ -270,9 +270,10 @@ int hdcg_coarse_apply(hdcg_t h, const void* x, void* y);
 
 /* Y = A X for nrhs (1..16) coarse vectors at once (Sec. 5.1 stencil, one read of
  * A for all of them).  x, y: canonical [nrhs][Vc][Nvec] complex double, device.
- * An FP16 operator runs on the tensor cores (tcgen05, FP32 accumulation; X
+ * FP16 and FP32 operators (Nvec <= 64) run on the tensor cores (tcgen05,
+ * FP32 accumulation; an FP32 A as an FP16 hi + lo pair, two MMAs per tile; X
  * enters as a scaled FP16 hi + lo pair per value, about 22 significant bits),
- * FP32/FP64 operators on the CUDA cores.  HDCG_ERR_TIMEOUT if a device-side
+ * FP64 operators on the CUDA cores.  HDCG_ERR_TIMEOUT if a device-side
  * pipeline wait expired.  Synchronous. */
 int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
 
@@ -446,6 +447,13 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
  * and r - H z), ms[2] FP64 true-residual H applies, ms[3] coarse CG, ms[4]
  * restriction and prolongation, ms[5] whole solves.  Synchronises the stream. */
 int hdcg_get_phase_profile(hdcg_t h, double ms[6]);
+/* Measurement: the mean device time (microseconds, CUDA events on the
+ * handle's stream) of one tensor-core little Dirac stencil apply (k_capply_tc,
+ * Sec. 5.1) of the level-1 operator to nrhs (1..16) Gaussian coarse vectors,
+ * after 3 warm-up launches, over reps launches.  HDCG_ERR_ARG unless A is FP16
+ * or FP32 with Nvec <= 64.  Synchronous. */
+int hdcg_time_coarse_apply(hdcg_t h, int nrhs, int reps, double* us_per_apply);
+
 /* The fine operator's hop passes come in variants: 0-2 scalar FP32 arithmetic
  * with register budgets for 1, 2 and 3 resident CTAs per SM; 3 all eight
  * neighbours prefetched (16-bit storage) or double-float arithmetic (FP64

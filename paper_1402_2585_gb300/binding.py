@@ -88,6 +88,7 @@ _SIGS = {
     "hdcg_build_subspace": (_I, [_P, ctypes.POINTER(SubspaceParams)]),
     "hdcg_set_subspace": (_I, [_P, _I, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
     "hdcg_promote_subspace": (_I, [_P, _P, _I]),
+    "hdcg_time_coarse_apply": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "hdcg_get_subspace": (_I, [_P, _I, _P]),
     "hdcg_build_coarse": (_I, [_P, _I, _I]),
     "hdcg_get_coarse": (_I, [_P, _I, _P]),
@@ -269,6 +270,12 @@ class Hdcg:
 
     def coarse_apply(self, x, y):
         return self._check(self._L.hdcg_coarse_apply(self.h, _ptr(x), _ptr(y)))
+
+    def time_coarse_apply(self, nrhs, reps=20):
+        """Mean device microseconds of one tensor-core stencil apply to nrhs vectors."""
+        us = ctypes.c_double(0.0)
+        self._check(self._L.hdcg_time_coarse_apply(self.h, int(nrhs), int(reps), ctypes.byref(us)))
+        return us.value
 
     def coarse_apply_multi(self, x, y, nrhs):
         return self._check(self._L.hdcg_coarse_apply_multi(self.h, _ptr(x), _ptr(y), int(nrhs)))

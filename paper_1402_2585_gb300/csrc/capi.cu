@@ -15,6 +15,7 @@ void build_subspace(Ctx& c, const hdcg_subspace_params& p);
 void build_subspace_rational(Ctx& c, const hdcg_subspace_params& p);
 void continue_subspace(Ctx& c, const hdcg_subspace_params& p);
 void promote_subspace(Ctx& c, Ctx& src, int prec);
+double coarse_tc_time_us(Ctx& c, Coarse& A, int R, int reps);
 void build_coarse(Ctx& c, int prec);
 void prep_source(Ctx& c, const void* eta_e, const void* eta_o, void* b);
 void reconstruct(Ctx& c, const void* eta_e, const void* psi_o, void* psi_e);
@@ -605,6 +606,15 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
     if (total_ms) *total_ms = c.prof.ms[prec];
     if (bytes) *bytes = c.prof.bytes[prec];
     if (op_bytes) *op_bytes = c.prof.op_bytes[prec];
+  });
+  return HDCG_OK;
+}
+
+int hdcg_time_coarse_apply(hdcg_t h, int nrhs, int reps, double* us_per_apply) {
+  HDCG_ENTRY(h, {
+    check_ptr(us_per_apply, "us_per_apply");
+    HDCG_REQUIRE(c.coarse, HDCG_ERR_STATE, "no coarse operator");
+    *us_per_apply = coarse_tc_time_us(c, *c.coarse, nrhs, reps);
   });
   return HDCG_OK;
 }

@@ -776,6 +776,38 @@ int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, dou
   return it;
 }
 
+// Mean device time of one tensor-core stencil apply (k_capply_tc alone) to R
+// Gaussian coarse vectors: 3 warm-up launches, then reps launches between two
+// CUDA events on the handle's stream (the B operand is prepared once).
+double coarse_tc_time_us(Ctx& c, Coarse& A, int R, int reps) {
+  HDCG_REQUIRE(coarse_tc_supported(A), HDCG_ERR_ARG, "the tensor-core apply needs an FP16 or FP32 A, Nvec <= 64");
+  HDCG_REQUIRE(R >= 1 && R <= RMAX && reps >= 1, HDCG_ERR_ARG, "1..16 right-hand sides, reps >= 1");
+  coarse_tc_prepare(c, A);
+  const size_t ne = A.Vc * A.nvec, nc = ne * R;
+  DevMem tmp;
+  tmp.ensure(2 * nc * sizeof(float2));
+  float2* xi = tmp.as<float2>();
+  float2* yi = xi + nc;
+  coarse_noise(c, xi, nc, 0x7e57);
+  unsigned* xmax = A.tcs.as<TcState>()->xmax;
+  coarse_tc_max(c, xi, ne, R, xmax);
+  coarse_tc_to_b(c, A, R, xi, xmax, nullptr);
+  for (int i = 0; i < 3; ++i) coarse_tc_apply(c, A, R, xi, yi, xmax, nullptr, nullptr, 0.0);
+  cudaEvent_t e0, e1;
+  HDCG_CUDA(cudaEventCreate(&e0));
+  HDCG_CUDA(cudaEventCreate(&e1));
+  HDCG_CUDA(cudaEventRecord(e0, c.stream));
+  for (int i = 0; i < reps; ++i) coarse_tc_apply(c, A, R, xi, yi, xmax, nullptr, nullptr, 0.0);
+  HDCG_CUDA(cudaEventRecord(e1, c.stream));
+  HDCG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  HDCG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  coarse_tc_check(c, A);
+  return 1e3 * ms / reps;
+}
+
 void coarse_apply_multi_canon(Ctx& c, Coarse& A, int R, const void* x64, void* y64) {
   HDCG_REQUIRE(R >= 1 && R <= RMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   const size_t ne = A.Vc * A.nvec, nc = ne * R;
