@@ -103,7 +103,12 @@ struct TcState {
 };
 struct TcGeom {
   int sites, MS, Kp, Rp, NS, NMMA, ncols, stages, parts;
-  uint32_t a_bytes, b_bytes, stage_bytes;   // a_bytes: one FP16 part of one block
+  // one FP16 part of one block of A: a_gbytes stored (and copied per stage),
+  // a_sbytes its shared-memory slot; lbo_a / sbo_a the distances between core
+  // matrices adjacent in K / in M; rows, kgs the stored row count and 8-wide
+  // K groups
+  uint32_t a_gbytes, a_sbytes, lbo_a, sbo_a, b_bytes, stage_bytes, copy_bytes;
+  int rows, kgs;
 };
 TcGeom tc_geom(int nvec, int R, int parts);
 bool coarse_tc_supported(const Coarse& A);

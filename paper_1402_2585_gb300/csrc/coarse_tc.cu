@@ -85,10 +85,36 @@ TcGeom tc_geom(int nvec, int R, int parts) {
   g.NMMA = g.sites * g.NS;
   g.ncols = 32;
   while (g.ncols < g.NMMA) g.ncols *= 2;
-  g.a_bytes = (uint32_t)g.MS * g.Kp * 2;
   g.b_bytes = (uint32_t)g.NS * g.Kp * 2;
   g.parts = parts;
-  g.stage_bytes = g.sites * (parts * g.a_bytes + g.b_bytes);
+  if (g.sites == 2) {
+    // two sites share the M = 128 rows: each block stored whole (MS x Kp),
+    // core matrices K-adjacent 128 B apart and M-adjacent 16 Kp B apart
+    g.rows = g.MS;
+    g.kgs = g.Kp / 8;
+    g.a_gbytes = (uint32_t)g.MS * g.Kp * 2;
+    g.a_sbytes = g.a_gbytes;
+    g.lbo_a = 128;
+    g.sbo_a = (uint32_t)g.Kp * 16;
+  } else {
+    // one site: only the 2 Nvec rows (in 8-row groups) and the Nvec columns
+    // (in 8-wide K groups) are stored, K group by K group (M-adjacent core
+    // matrices 128 B apart, K-adjacent RG 128 B apart), so a stage copies
+    // exactly the operator's bytes.  The MMA reads 16 row groups and Kp / 8
+    // K groups: rows past 2 Nvec come from the next K group (finite values;
+    // their output rows are discarded), and the K groups past Nvec from the
+    // slot's tail, which no copy writes and which stays zero (the kernel
+    // clears the ring once).
+    const int RG = (2 * nvec + 7) / 8;
+    g.rows = 8 * RG;
+    g.kgs = (nvec + 7) / 8;
+    g.a_gbytes = (uint32_t)(g.kgs * RG * 128);
+    g.a_sbytes = (uint32_t)(((g.Kp / 8 - 1) * RG + 16) * 128);
+    g.lbo_a = (uint32_t)RG * 128u;
+    g.sbo_a = 128;
+  }
+  g.stage_bytes = g.sites * (parts * g.a_sbytes + g.b_bytes);
+  g.copy_bytes = g.sites * (parts * g.a_gbytes + g.b_bytes);
   g.stages = (int)std::min<uint32_t>(16, TC_RING_BYTES / g.stage_bytes);
   g.stages = std::max(g.stages, 2);
   return g;
@@ -119,13 +145,14 @@ __global__ void k_site_scale(const AT* __restrict__ A, int n, int* sexp) {
 }
 
 // A ([a][l][k][j] complex, FP16 or FP32) -> tiled operand, one 16-byte row segment per
-// thread: element (m, k) of part p of block (a, l) at byte p a_bytes + (m/8)(16 Kp) +
-// (k/8) 128 + (m%8) 16 + (k%8) 2, a_bytes = MS Kp 2; part 0 = hi, part 1 = lo.
+// thread: element (m, k) (m < rows, k < 8 kgs) of part p of block (a, l) at byte
+// (blk parts + p) a_gbytes + (m/8) sbo + (k/8) lbo + (m%8) 16 + (k%8) 2; part 0 = hi,
+// part 1 = lo.
 template <typename AT>
-__global__ void k_a_to_tc(const AT* __restrict__ A, uint4* __restrict__ Atc, size_t nblk, int n, int MS, int Kp,
-                          int parts, const int* __restrict__ sexp) {
-  const int KG = Kp / 8;
-  const size_t per = (size_t)MS * KG;
+__global__ void k_a_to_tc(const AT* __restrict__ A, uint4* __restrict__ Atc, size_t nblk, int n, int rows, int kgs,
+                          uint32_t a_gbytes, uint32_t lbo, uint32_t sbo, int parts, const int* __restrict__ sexp) {
+  const int KG = kgs;
+  const size_t per = (size_t)rows * KG;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nblk * per) return;
   const size_t blk = t / per;
@@ -146,11 +173,10 @@ __global__ void k_a_to_tc(const AT* __restrict__ A, uint4* __restrict__ Atc, siz
     hi[q] = __float2half_rn(x);
     lo[q] = __float2half_rn(x - __half2float(hi[q]));
   }
-  const size_t a_bytes = (size_t)MS * Kp * 2;
-  char* dst = reinterpret_cast<char*>(Atc) + blk * parts * a_bytes + (size_t)(m / 8) * (Kp * 16) + kg * 128 +
-              (m % 8) * 16;
+  char* dst = reinterpret_cast<char*>(Atc) + blk * parts * (size_t)a_gbytes + (size_t)(m / 8) * sbo +
+              (size_t)kg * lbo + (m % 8) * 16;
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(hi);
-  if (parts == 2) *reinterpret_cast<uint4*>(dst + a_bytes) = *reinterpret_cast<const uint4*>(lo);
+  if (parts == 2) *reinterpret_cast<uint4*>(dst + a_gbytes) = *reinterpret_cast<const uint4*>(lo);
 }
 
 // X (FP32 complex [a][k][r]) -> tiled B operand of every coarse site: thread
@@ -222,7 +248,7 @@ struct TcArgs {
   const int* skip;     // nonzero: the launch has nothing to do (nullable)
   unsigned* err;       // bit flags of expired waits
   int Vc, n, R, sites, MS, Kp, NS, stages, ncols;
-  uint32_t a_bytes, b_bytes, idesc;
+  uint32_t a_gbytes, a_sbytes, lbo_a, sbo_a, b_bytes, copy_bytes, idesc;
   float shift;         // Y = (A + shift) X (needs x)
   int parts;           // 1: FP16 operator, 2: FP32 operator as FP16 hi + lo
   const int* sexp;     // per-site scale exponents of the tiled operator
@@ -232,8 +258,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
   extern __shared__ __align__(128) unsigned char smem[];
   if (g.skip && *g.skip) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t stage_bytes = g.sites * (g.parts * g.a_bytes + g.b_bytes);
+  const uint32_t stage_bytes = g.sites * (g.parts * g.a_sbytes + g.b_bytes);
   const uint32_t ring = tc::smem_u32(smem);
+  // clear the ring once: the tails of the A slots that no copy writes are read
+  // by the MMAs as K padding and must be zero
+  for (uint32_t i = threadIdx.x; i < (uint32_t)g.stages * stage_bytes / 16u; i += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  tc::fence_proxy_async_smem();
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * stage_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * g.stages + 3);
   const uint32_t bar0 = tc::smem_u32(bars);
@@ -286,19 +317,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
             atomicOr(g.err, 1u);
             break;
           }
-          tc::mbar_arrive_expect_tx(TC_FULL(s), stage_bytes);
+          tc::mbar_arrive_expect_tx(TC_FULL(s), g.copy_bytes);
           const uint32_t dst = ring + (uint32_t)s * stage_bytes;
           // stage: [part 0: site 0, site 1][part 1: site 0, site 1][B site 0][B site 1]
           for (int pp = 0; pp < g.parts; ++pp)
             for (int si = 0; si < g.sites; ++si) {
               const size_t blk = (size_t)(si ? s1 : s0) * 81 + l;
-              tc::bulk_g2s(dst + (pp * g.sites + si) * g.a_bytes,
-                           reinterpret_cast<const char*>(g.Atc) + (blk * g.parts + pp) * g.a_bytes, g.a_bytes,
+              tc::bulk_g2s(dst + (pp * g.sites + si) * g.a_sbytes,
+                           reinterpret_cast<const char*>(g.Atc) + (blk * g.parts + pp) * g.a_gbytes, g.a_gbytes,
                            TC_FULL(s));
             }
           for (int si = 0; si < g.sites; ++si) {
             const int nb = snb[si * 81 + l];
-            tc::bulk_g2s(dst + g.sites * g.parts * g.a_bytes + si * g.b_bytes,
+            tc::bulk_g2s(dst + g.sites * g.parts * g.a_sbytes + si * g.b_bytes,
                          reinterpret_cast<const char*>(g.xtc) + (size_t)nb * g.b_bytes, g.b_bytes, TC_FULL(s));
           }
         }
@@ -336,11 +367,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_capply_tc(TcArgs g, Reduction
           }
           tc::fence_after_sync();
           const uint32_t abase = ring + (uint32_t)s * stage_bytes;
-          const uint32_t bbase = abase + g.sites * g.parts * g.a_bytes;
+          const uint32_t bbase = abase + g.sites * g.parts * g.a_sbytes;
           for (int ks = 0; ks < g.Kp / 16; ++ks) {
             const uint64_t bd = tc::smem_desc(bbase + 256u * ks, 128u, sbo);
             for (int p = 0; p < g.parts; ++p) {
-              const uint64_t ad = tc::smem_desc(abase + p * g.sites * g.a_bytes + 256u * ks, 128u, sbo);
+              const uint64_t ad =
+                  tc::smem_desc(abase + p * g.sites * g.a_sbytes + 2u * g.lbo_a * ks, g.lbo_a, g.sbo_a);
               tc::mma_f16(tmem, ad, bd, g.idesc, (l | ks | p) != 0 ? 1u : 0u);
             }
           }
@@ -426,20 +458,21 @@ void coarse_tc_prepare(Ctx& c, Coarse& A) {
   const int parts = tc_parts(A);
   const TcGeom g = tc_geom(A.nvec, 1, parts);
   const size_t nblk = A.Vc * 81;
-  A.Atc.ensure(nblk * parts * g.a_bytes);
+  A.Atc.ensure(nblk * parts * g.a_gbytes);
   A.sexp.ensure(A.Vc * sizeof(int));
   A.tcs.ensure(sizeof(TcState));
   HDCG_CUDA(cudaMemsetAsync(A.tcs.p, 0, sizeof(TcState), c.stream));
-  const size_t nt = nblk * g.MS * (g.Kp / 8);
+  const size_t nt = nblk * g.rows * g.kgs;
   if (A.prec == HDCG_F32) {
     k_site_scale<float2><<<(unsigned)A.Vc, 256, 0, c.stream>>>(A.A.as<float2>(), A.nvec, A.sexp.as<int>());
-    k_a_to_tc<float2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(A.A.as<float2>(), A.Atc.as<uint4>(), nblk,
-                                                                          A.nvec, g.MS, g.Kp, parts, A.sexp.as<int>());
+    k_a_to_tc<float2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(
+        A.A.as<float2>(), A.Atc.as<uint4>(), nblk, A.nvec, g.rows, g.kgs, g.a_gbytes, g.lbo_a, g.sbo_a, parts,
+        A.sexp.as<int>());
   } else {
     k_site_scale<__half2><<<(unsigned)A.Vc, 256, 0, c.stream>>>(A.A.as<__half2>(), A.nvec, A.sexp.as<int>());
-    k_a_to_tc<__half2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(A.A.as<__half2>(), A.Atc.as<uint4>(),
-                                                                           nblk, A.nvec, g.MS, g.Kp, parts,
-                                                                           A.sexp.as<int>());
+    k_a_to_tc<__half2><<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(
+        A.A.as<__half2>(), A.Atc.as<uint4>(), nblk, A.nvec, g.rows, g.kgs, g.a_gbytes, g.lbo_a, g.sbo_a, parts,
+        A.sexp.as<int>());
   }
   HDCG_CUDA(cudaGetLastError());
   c.launches += 2;
@@ -495,7 +528,11 @@ void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const
   a.NS = g.NS;
   a.stages = g.stages;
   a.ncols = g.ncols;
-  a.a_bytes = g.a_bytes;
+  a.a_gbytes = g.a_gbytes;
+  a.a_sbytes = g.a_sbytes;
+  a.lbo_a = g.lbo_a;
+  a.sbo_a = g.sbo_a;
+  a.copy_bytes = g.copy_bytes;
   a.b_bytes = g.b_bytes;
   a.idesc = tc::idesc_f16_f32(128, g.NMMA);
   a.shift = (float)shift;
