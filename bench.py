@@ -360,6 +360,7 @@ def run_ours(args, w):
     clk.start()
     launches0 = h.launch_count()
     times, stats = [], []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -371,6 +372,7 @@ def run_ours(args, w):
         torch.cuda.synchronize(dev)
         times.append(e0.elapsed_time(e1) / 1e3)
         stats.append(st.as_dict())
+    torch.cuda.nvtx.range_pop()
     launches = h.launch_count() - launches0
     clocks = clk.stop()
     t_solve = max_over_ranks(statistics.mean(times), world, dev)
@@ -618,7 +620,8 @@ def run_coarse_only(args, w):
     h.set_dwf(w.M5, w.b, w.c, w.mass)
     h.set_gauge(torch.from_numpy(sy.gauge_field(w.dims, w.eps, w.gauge_seed)).to(dev))
     h.build_subspace(w.block, w.nvec, sub_prec, inv_steps=0, seed=w.subspace_seed)
-    h.build_coarse(PREC[args.coarse_prec] if args.coarse_prec else sub_prec)
+    cp = args.coarse_prec or w.coarse_prec
+    h.build_coarse(PREC[cp] if cp else sub_prec)
     vc = 1
     for d, b in zip(w.dims, w.block):
         vc *= d // b
@@ -648,7 +651,7 @@ def run_coarse_only(args, w):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     print(json.dumps({"workload": w.name, "coarse_applies": args.coarse_only, "rhs": R or 1,
-                      "coarse_storage": args.coarse_prec or w.prec,
+                      "coarse_storage": cp or w.prec,
                       "ms_per_call_device": e0.elapsed_time(e1) / args.coarse_only,
                       "ms_per_call_host": (time.perf_counter() - t0) * 1e3 / args.coarse_only}), flush=True)
 

@@ -89,6 +89,12 @@ WORKLOADS = {
     # Profiling case for the coarse level: the 24^3 x 48 coarse grid and Nvec of
     # cfg3 (an 860 MB FP16 little Dirac operator, larger than L2) over Ls = 2,
     # so the fine subspace stays near 1 GB.
+    # Profiling case for the one-site tensor-core tiles: Nvec 40 (the first
+    # level of the three-level workload) on a 4^3 x 8 coarse grid (512 sites;
+    # a 531 MB FP32 operator, above L2) over Ls = 2.
+    "prof_coarse_16x16x16x32_ls2_nvec40": Workload(
+        "prof_coarse_16x16x16x32_ls2_nvec40", (16, 16, 16, 32), 2, 1.8, 1.5, 0.5, 0.001, 0.45,
+        (4, 4, 4, 4), 40, 1e-8, "f16", seed=7, coarse_prec="f32"),
     "prof_coarse_24x24x24x48_ls2": Workload(
         "prof_coarse_24x24x24x48_ls2", (24, 24, 24, 48), 2, 1.8, 1.5, 0.5, 0.002, 0.4,
         (4, 4, 4, 4), 32, 1e-8, "f16", seed=6),
