@@ -53,12 +53,17 @@ PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 # property of the algorithm on that input).  The reference arm, which runs no
 # GPU code, scales the oracle's per-apply time by it; the GPU arm reports its
 # measured count beside this figure (``h_applies_per_rhs``).
-H_APPLIES_PER_RHS = {DEFAULT_WORKLOAD: 900, "cfg2_16x16x16x16_ls16_shamir": 140}
+H_APPLIES_PER_RHS = {DEFAULT_WORKLOAD: 1211, "cfg2_16x16x16x16_ls16_shamir": 140}
 
 # DRAM bytes (read + write) per hop_kernel launch of the outer precision from
 # one ncu capture of the current kernel, per workload; None once the kernel
 # changes (the counters then no longer describe it).
-HOP_TRAFFIC = {}
+HOP_TRAFFIC = {
+    # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the four FP16 passes
+    # of one H at this size (bench.py --apply-only 3, no fused CG epilogue),
+    # averaged per launch: 2.19, 3.32, 2.14 and 3.33 GB for passes A-D
+    DEFAULT_WORKLOAD: 2.745e9,
+}
 
 
 def hop_flops_per_site(w) -> int:
@@ -275,11 +280,16 @@ def build_levels(h, w, seeds, args):
     if w.block2 and not args.two_level:
         t0 = time.perf_counter()
         h.build_subspace(w.block2, w.nvec2, 1, inv_steps=w.inv2_steps, inv_shift=0.0, inv_tol=w.inv2_tol,
-                         inv_maxiter=20000, seed=seeds["subspace"] + 11, level=2)
+                         inv_maxiter=w.inv2_maxiter, seed=seeds["subspace"] + 11, level=2)
         out["level2_subspace"] = time.perf_counter() - t0
         t0 = time.perf_counter()
         h.build_coarse(1, level=2)
         out["level2_operator"] = time.perf_counter() - t0
+        if w.qtrunc_order:
+            t0 = time.perf_counter()
+            lo, hi = h.set_coarse_preconditioner(w.qtrunc_order)
+            out["qtrunc_chebyshev"] = {"seconds": time.perf_counter() - t0, "order": w.qtrunc_order,
+                                       "interval": [lo, hi]}
     ldop = args.ldop_nvec if args.ldop_nvec is not None else w.ldop_nvec
     if ldop and (not w.block2 or args.two_level):
         t0 = time.perf_counter()
@@ -564,7 +574,10 @@ def roofline(w, hop_all, pname, peak, peak_kind, nrhs):
     b_fused = hp["bytes"] / hp["launches"]
     b_op = hp["op_bytes"] / hp["launches"]
     return {"bound": "hbm", "achieved": b_fused / per_launch_s / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": b_fused / per_launch_s / 1e9 / peak, "traffic": HOP_TRAFFIC.get(w.name),
+            "frac": b_fused / per_launch_s / 1e9 / peak,
+            "traffic": HOP_TRAFFIC.get(w.name) if pname == "f16" else None,
+            "traffic_note": ("ncu, unfused operator passes of one H at this size, mean per launch"
+                             if HOP_TRAFFIC.get(w.name) and pname == "f16" else None),
             "kernel": f"hop_kernel ({pname} storage, 4 passes per H)", "launches": hp["launches"],
             "avg_launch_us": per_launch_s * 1e6, "bytes_per_launch": b_fused,
             "achieved_operator_bytes_only": b_op / per_launch_s / 1e9,

@@ -41,6 +41,10 @@ class Workload:
     inv_maxiter: int = 20000
     inv2_steps: int = 2
     inv2_tol: float = 1e-3
+    inv2_maxiter: int = 20000
+    # order of the Chebyshev polynomial of Q_trunc smoothing the level-1 solve
+    # of a three-level workload (0: none; interval from the power iteration)
+    qtrunc_order: int = 0
     # storage of the little Dirac operator (None: FP64 for FP64 storage, FP32 for
     # FP32, FP16 for 16-bit); at m = 0.001 an FP16 operator is not positive
     # definite at the bottom of its spectrum, so the three-level workload keeps FP32
@@ -85,7 +89,7 @@ WORKLOADS = {
     "cfg5_32x32x32x64_ls16_mobius_3lvl": Workload(
         "cfg5_32x32x32x64_ls16_mobius_3lvl", (32, 32, 32, 64), 16, 1.8, 1.5, 0.5, 0.001, 0.45,
         (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=5,
-        inv_steps=2, inv_tol=1e-3, inv_maxiter=150, coarse_prec="f32"),
+        inv_steps=2, inv_tol=1e-3, inv_maxiter=150, coarse_prec="f32", qtrunc_order=8),
     # Profiling case for the coarse level: the 24^3 x 48 coarse grid and Nvec of
     # cfg3 (an 860 MB FP16 little Dirac operator, larger than L2) over Ls = 2,
     # so the fine subspace stays near 1 GB.
