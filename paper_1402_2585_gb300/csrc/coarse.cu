@@ -592,6 +592,7 @@ void coarse_init(Ctx& c, Coarse& A, const Subspace& s, int prec) {
   A.prec = prec;
   A.tc_ready = false;
   A.tc_choice = -1;
+  for (int& v : A.tc_cfg) v = 0;
   A.defl.nd = 0;            // a deflation space belongs to the operator it was built for
   A.defl.lam_h.clear();
   A.graph_cg.reset();
@@ -703,6 +704,7 @@ __global__ void k_fourier_solve(const double2* __restrict__ F, const double2* __
 void coarse_assemble(Ctx& c, Coarse& A, const Subspace& s, int hprec) {
   A.tc_ready = false;
   A.tc_choice = -1;
+  for (int& v : A.tc_cfg) v = 0;
   const int n = s.nvec;
   // per-dimension offsets and momenta; compact index q = qx + nx (qy + ny (qz + nz qt))
   std::vector<int> offs[4], moms[4];
@@ -1306,6 +1308,7 @@ void coarse_import(Ctx& c, Coarse& A, const void* src, int on_device) {
   ++c.launches;
   A.tc_ready = false;
   A.tc_choice = -1;
+  for (int& v : A.tc_cfg) v = 0;
   HDCG_CUDA(cudaStreamSynchronize(c.stream));
 }
 

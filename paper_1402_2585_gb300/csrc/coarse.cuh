@@ -73,6 +73,7 @@ struct Coarse {
   bool tc_ready = false;
   CapturedGraph graph_cg, graph_ad1;   // captured iteration pairs of the coarse solvers
   int tc_choice = -1;       // single right-hand side: -1 undecided, 0 CUDA cores, 1 tensor cores
+  int tc_cfg[RMAX + 1] = {};  // tensor-core apply to R vectors: CTAs per SM (1 or 2), 0 undecided
   // second-level (global) deflation space of A, prediagonalised: Z^dag A Z = diag(lam)
   struct Defl {
     int nd = 0;
@@ -110,7 +111,8 @@ struct TcGeom {
   uint32_t a_gbytes, a_sbytes, lbo_a, sbo_a, b_bytes, stage_bytes, copy_bytes;
   int rows, kgs;
 };
-TcGeom tc_geom(int nvec, int R, int parts);
+// ring_bytes: the shared-memory pipeline of one CTA (two CTAs per SM: 96 KB; one: 192 KB)
+TcGeom tc_geom(int nvec, int R, int parts, uint32_t ring_bytes = 96 * 1024);
 bool coarse_tc_supported(const Coarse& A);
 void coarse_tc_prepare(Ctx& c, Coarse& A);
 // coarse CG on R right-hand sides (FP32 vectors [a][k][r]) with the tensor-core operator

@@ -47,6 +47,7 @@ namespace {
 constexpr int TC_THREADS = 192;
 constexpr int TC_RPMAX = RMAX;                 // right-hand sides per launch
 constexpr uint32_t TC_RING_BYTES = 96 * 1024;  // two CTAs per SM
+constexpr uint32_t TC_RING_BYTES_1 = 192 * 1024;  // one CTA per SM
 
 int device_sms() {
   static int n = 0;
@@ -72,7 +73,7 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) 
 
 }  // namespace
 
-TcGeom tc_geom(int nvec, int R, int parts) {
+TcGeom tc_geom(int nvec, int R, int parts, uint32_t ring_bytes) {
   HDCG_REQUIRE(nvec >= 1 && nvec <= 64, HDCG_ERR_ARG, "tensor-core coarse operator needs Nvec <= 64");
   HDCG_REQUIRE(R >= 1 && R <= TC_RPMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   TcGeom g;
@@ -115,7 +116,7 @@ TcGeom tc_geom(int nvec, int R, int parts) {
   }
   g.stage_bytes = g.sites * (parts * g.a_sbytes + g.b_bytes);
   g.copy_bytes = g.sites * (parts * g.a_gbytes + g.b_bytes);
-  g.stages = (int)std::min<uint32_t>(16, TC_RING_BYTES / g.stage_bytes);
+  g.stages = (int)std::min<uint32_t>(16, ring_bytes / g.stage_bytes);
   g.stages = std::max(g.stages, 2);
   return g;
 }
@@ -507,9 +508,10 @@ void coarse_tc_to_b(Ctx& c, Coarse& A, int R, const float2* x, const unsigned* x
   ++c.launches;
 }
 
-void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
-                     double* dot_result, double shift) {
-  const TcGeom g = tc_geom(A.nvec, R, tc_parts(A));
+// one launch with cpsm (1 or 2) persistent CTAs per SM and the matching ring
+static void launch_tc(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
+                      double* dot_result, double shift, int cpsm) {
+  const TcGeom g = tc_geom(A.nvec, R, tc_parts(A), cpsm == 1 ? TC_RING_BYTES_1 : TC_RING_BYTES);
   TcArgs a;
   a.Atc = A.Atc.as<uint4>();
   a.cnbr = A.cnbr.as<int>();
@@ -545,11 +547,50 @@ void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const
     smem_set = std::max<size_t>(smem, 100 * 1024);
   }
   const int npairs = (int)((A.Vc + g.sites - 1) / g.sites);
-  const unsigned grid = (unsigned)std::min(npairs, 2 * device_sms());
+  const unsigned grid = (unsigned)std::min(npairs, cpsm * device_sms());
   const Reduction red = dot_result ? make_reduction(c, grid, RMAX, dot_result, 0) : Reduction{};
   k_capply_tc<<<grid, TC_THREADS, smem, c.stream>>>(a, red);
   HDCG_CUDA(cudaGetLastError());
   ++c.launches;
+}
+
+// The first apply to R vectors of an operator times two persistent shapes, two
+// CTAs per SM with a 96 KB ring and one CTA per SM with a 192 KB ring (twice
+// the stages in flight), and keeps the faster.  Both run the same MMAs in the
+// same order, so the choice never changes a result.  Inside a stream capture
+// the two-CTA shape runs untimed.
+void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
+                     double* dot_result, double shift) {
+  int cfg = A.tc_cfg[R];
+  if (cfg == 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HDCG_CUDA(cudaStreamIsCapturing(c.stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone || c.tuning_off) {
+      cfg = 2;
+    } else {
+      cudaEvent_t e0, e1;
+      HDCG_CUDA(cudaEventCreate(&e0));
+      HDCG_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int cand : {2, 1}) {
+        launch_tc(c, A, R, x, y, xmax, skip, dot_result, shift, cand);
+        HDCG_CUDA(cudaEventRecord(e0, c.stream));
+        for (int i = 0; i < 3; ++i) launch_tc(c, A, R, x, y, xmax, skip, dot_result, shift, cand);
+        HDCG_CUDA(cudaEventRecord(e1, c.stream));
+        HDCG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HDCG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          cfg = cand;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      A.tc_cfg[R] = cfg;
+    }
+  }
+  launch_tc(c, A, R, x, y, xmax, skip, dot_result, shift, cfg);
 }
 
 // ---------------------------------------------------------------------------------
