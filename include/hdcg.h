@@ -447,6 +447,13 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
  * and r - H z), ms[2] FP64 true-residual H applies, ms[3] coarse CG, ms[4]
  * restriction and prolongation, ms[5] whole solves.  Synchronises the stream. */
 int hdcg_get_phase_profile(hdcg_t h, double ms[6]);
+/* The tensor-core stencil runs as a persistent kernel with two CTAs per SM
+ * (96 KB pipeline ring each) or one (192 KB ring).  By default (0) the first
+ * apply of each operator to a given number of right-hand sides times both and
+ * keeps the faster; 1 or 2 forces one.  Both run the same MMAs in the same
+ * order, so the results are identical.  HDCG_ERR_ARG outside 0..2. */
+int hdcg_set_coarse_tc_shape(hdcg_t h, int ctas_per_sm);
+
 /* Measurement: the mean device time (microseconds, CUDA events on the
  * handle's stream) of one tensor-core little Dirac stencil apply (k_capply_tc,
  * Sec. 5.1) of the level-1 operator to nrhs (1..16) Gaussian coarse vectors,

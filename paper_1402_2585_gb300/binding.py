@@ -89,6 +89,7 @@ _SIGS = {
     "hdcg_set_subspace": (_I, [_P, _I, ctypes.POINTER(_I), _I, _I, _P, _I, _I]),
     "hdcg_promote_subspace": (_I, [_P, _P, _I]),
     "hdcg_time_coarse_apply": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "hdcg_set_coarse_tc_shape": (_I, [_P, _I]),
     "hdcg_get_subspace": (_I, [_P, _I, _P]),
     "hdcg_build_coarse": (_I, [_P, _I, _I]),
     "hdcg_get_coarse": (_I, [_P, _I, _P]),
@@ -270,6 +271,10 @@ class Hdcg:
 
     def coarse_apply(self, x, y):
         return self._check(self._L.hdcg_coarse_apply(self.h, _ptr(x), _ptr(y)))
+
+    def set_coarse_tc_shape(self, ctas_per_sm):
+        """0: autotune the tensor-core stencil's persistent shape; 1 or 2: force it."""
+        return self._check(self._L.hdcg_set_coarse_tc_shape(self.h, int(ctas_per_sm)))
 
     def time_coarse_apply(self, nrhs, reps=20):
         """Mean device microseconds of one tensor-core stencil apply to nrhs vectors."""

@@ -610,6 +610,14 @@ int hdcg_get_hop_profile(hdcg_t h, int prec, long long* launches, double* total_
   return HDCG_OK;
 }
 
+int hdcg_set_coarse_tc_shape(hdcg_t h, int ctas_per_sm) {
+  HDCG_ENTRY(h, {
+    HDCG_REQUIRE(ctas_per_sm >= 0 && ctas_per_sm <= 2, HDCG_ERR_ARG, "ctas_per_sm must be 0, 1 or 2");
+    c.tc_force = ctas_per_sm;
+  });
+  return HDCG_OK;
+}
+
 int hdcg_time_coarse_apply(hdcg_t h, int nrhs, int reps, double* us_per_apply) {
   HDCG_ENTRY(h, {
     check_ptr(us_per_apply, "us_per_apply");

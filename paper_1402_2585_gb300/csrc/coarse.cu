@@ -1185,10 +1185,6 @@ static int coarse_cg_t(Ctx& c, Coarse& A, const void* rhs, void* sol, double tol
 // CUDA-core and of the tensor-core coarse CG once per operator, keep the faster.
 static void tune_single(Ctx& c, Coarse& A, const void* rhs, void* sol) {
   coarse_tc_prepare(c, A);
-  if (c.tuning_off) {
-    A.tc_choice = 1;
-    return;
-  }
   const int keep = A.last_iters;
   cudaEvent_t e[3];
   for (auto& ev : e) HDCG_CUDA(cudaEventCreate(&ev));

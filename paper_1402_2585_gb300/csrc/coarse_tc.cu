@@ -561,11 +561,11 @@ static void launch_tc(Ctx& c, Coarse& A, int R, const float2* x, float2* y, cons
 // the two-CTA shape runs untimed.
 void coarse_tc_apply(Ctx& c, Coarse& A, int R, const float2* x, float2* y, const unsigned* xmax, const int* skip,
                      double* dot_result, double shift) {
-  int cfg = A.tc_cfg[R];
+  int cfg = c.tc_force ? c.tc_force : A.tc_cfg[R];
   if (cfg == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     HDCG_CUDA(cudaStreamIsCapturing(c.stream, &cs));
-    if (cs != cudaStreamCaptureStatusNone || c.tuning_off) {
+    if (cs != cudaStreamCaptureStatusNone) {
       cfg = 2;
     } else {
       cudaEvent_t e0, e1;

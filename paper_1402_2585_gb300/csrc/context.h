@@ -117,8 +117,8 @@ struct Ctx {
   DevMem links[5][2];     // per link slot (F64, F32, F16, BF16) and output parity
   DevMem scratch_f[NPREC][24]; // work fields per precision (slot roles: solver.cu; 20-23: hop autotuner)
   std::map<int, int> hop_tuned;  // (prec, pass, fused, reduction) -> chosen hop variant
-  bool tuning_off = false;
   int hop_force = -1;            // >= 0: every hop launch uses this variant (hdcg_set_hop_variant)
+  int tc_force = 0;              // 1, 2: the tensor-core stencil's CTAs per SM (hdcg_set_coarse_tc_shape)
   DevMem red_partials, red_ticket, scalars;
   DevMem canon_in, canon_out;  // canonical <-> internal staging
 

@@ -203,10 +203,6 @@ static int hop_variant(Ctx& c, int prec, int pass, bool mob, const HopArgs& a, d
   }
   auto it = c.hop_tuned.find(key);
   if (it != c.hop_tuned.end()) return it->second;
-  if (c.tuning_off) {
-    c.hop_tuned[key] = 0;
-    return 0;
-  }
   // scratch copies: inputs are whatever the scratch slots hold (only timing matters)
   HopArgs t = a;
   t.fstride = 0;

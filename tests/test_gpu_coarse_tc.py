@@ -166,3 +166,21 @@ def test_set_coarse_and_multi_apply_errors():
     with pytest.raises(HdcgError) as e:
         h2.coarse_apply_multi(x, torch.zeros_like(x), 17)
     assert e.value.code == -1           # at most 16 right-hand sides
+
+
+@pytest.mark.parametrize("nvec,prec", [(40, F32), (24, F16), (64, F16)])
+def test_persistent_shapes_give_identical_results(nvec, prec):
+    """One and two persistent CTAs per SM (ring depths 192 KB and 96 KB) run the
+    same MMAs in the same order: bit-identical outputs, both equal to the
+    oracle's apply; the autotuned default gives the same bits again."""
+    torch, bl, h, A = _handle("full_12x12x12x12_ls2", nvec, prec)
+    X = sy.complex_normal(940 + nvec, (12, bl.Vc, nvec))
+    out = {}
+    for shape in (1, 2, 0):
+        h.set_coarse_tc_shape(shape)
+        out[shape] = _multi(torch, h, X)
+    assert np.array_equal(out[1], out[2]) and np.array_equal(out[0], out[2])
+    for r in range(12):
+        assert rel(out[2][r], coarse_apply(A, X[r], bl)) < 1e-5, f"rhs {r}"
+    with pytest.raises(HdcgError):
+        h.set_coarse_tc_shape(3)
