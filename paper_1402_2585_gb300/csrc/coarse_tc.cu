@@ -20,14 +20,15 @@
 // operator is split into FP16 hi + lo parts (about 22 significant bits) that
 // enter as two MMAs against the same B tile; an FP16 operator is one part.
 //
-// With Nvec <= 32 a block has 2 Nvec <= 64 rows, so two coarse sites share
-// one M = 128 MMA (rows 0..63 site a0, 64..127 site a1) against B = [B_{a0+l}
-// | B_{a1+l}]; the two off-diagonal quadrants of D are discarded.  With
-// 32 < Nvec <= 64 one site fills M = 128.  K = Nvec padded to a multiple of
-// 16.  Both operands are pre-tiled in global memory in the no-swizzle K-major
-// core-matrix layout, so every stage of the pipeline is filled by plain bulk
-// copies: the A blocks of the sites (the HBM stream) and the B tiles of their
-// neighbours (L2-resident).
+// With Nvec = 32 a block has 64 rows, so two coarse sites share one M = 128
+// MMA (rows 0..63 site a0, 64..127 site a1) against B = [B_{a0+l} | B_{a1+l}];
+// the two off-diagonal quadrants of D are discarded.  Otherwise one site per
+// MMA: its 2 Nvec rows are stored and the MMA's remaining rows are discarded.
+// K = Nvec padded to a multiple of 16.  Both operands are pre-tiled in global
+// memory in the no-swizzle K-major core-matrix layout, so every stage of the
+// pipeline is filled by plain bulk copies: the A blocks of the sites (the HBM
+// stream, exactly the operator's bytes) and the B tiles of their neighbours
+// (L2-resident).
 //
 // Pipeline per CTA (persistent, up to two CTAs per SM): warp 0 issues the
 // copies into a ring of stages, warp 1 issues the MMAs (one accumulator in
@@ -77,7 +78,10 @@ TcGeom tc_geom(int nvec, int R, int parts, uint32_t ring_bytes) {
   HDCG_REQUIRE(nvec >= 1 && nvec <= 64, HDCG_ERR_ARG, "tensor-core coarse operator needs Nvec <= 64");
   HDCG_REQUIRE(R >= 1 && R <= TC_RPMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   TcGeom g;
-  g.sites = nvec <= 32 ? 2 : 1;
+  // two sites share an MMA only when they fill its 128 rows exactly (Nvec 32);
+  // otherwise one site per MMA with the compact layout below, which copies
+  // only the operator's bytes
+  g.sites = nvec == 32 ? 2 : 1;
   g.MS = 128 / g.sites;
   g.Kp = (nvec + 15) / 16 * 16;
   const int q = g.sites == 2 ? 2 : 4;   // keeps N = sites * 4 Rp a multiple of 16
