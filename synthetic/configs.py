@@ -93,6 +93,13 @@ WORKLOADS = {
     # Profiling case for the coarse level: the 24^3 x 48 coarse grid and Nvec of
     # cfg3 (an 860 MB FP16 little Dirac operator, larger than L2) over Ls = 2,
     # so the fine subspace stays near 1 GB.
+    # Launch-list case of the three-level path: the physical-point-like
+    # workload's action, blockings, Nvec and storage on a 16^3 x 32 lattice
+    # (1/8 of its volume), so the whole bench run stays within a few minutes.
+    "prof_3lvl_16x16x16x32_ls16_mobius": Workload(
+        "prof_3lvl_16x16x16x32_ls16_mobius", (16, 16, 16, 32), 16, 1.8, 1.5, 0.5, 0.001, 0.45,
+        (4, 4, 4, 4), 40, 1e-8, "f16", nrhs=12, block2=(2, 2, 2, 2), nvec2=24, seed=8,
+        inv_steps=2, inv_tol=1e-3, inv_maxiter=150, coarse_prec="f32", qtrunc_order=8),
     # Profiling case for the one-site tensor-core tiles: Nvec 40 (the first
     # level of the three-level workload) on a 4^3 x 8 coarse grid (512 sites;
     # a 531 MB FP32 operator, above L2) over Ls = 2.
