@@ -283,7 +283,10 @@ int hdcg_coarse_apply_multi(hdcg_t h, const void* x, void* y, int nrhs);
  * the second-level deflation space when one was built, otherwise CG (the inner
  * inversion of Q, Sec. 2).  b, x: canonical [nrhs][Vc][Nvec] complex double,
  * device; x is overwritten (zero start).  *iterations (nullable) receives the
- * lockstep iteration count.  Synchronous. */
+ * lockstep iteration count.  HDCG_ERR_BREAKDOWN if the level-2 A-DEF2 solve
+ * met (p, A p) <= 0 or a non-finite residual before the tolerance (inside
+ * hdcg_solve the preconditioner keeps that right-hand side's last iterate
+ * instead).  Synchronous. */
 int hdcg_coarse_solve(hdcg_t h, const void* b, void* x, int nrhs, double tol, int maxiter, int* iterations);
 
 /* y = A x exactly like hdcg_coarse_apply, but without allocating any device

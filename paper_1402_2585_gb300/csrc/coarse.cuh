@@ -43,6 +43,7 @@ struct Level2 {
   bool have_A2 = false;
   DevMem work, ctl;              // level-1 solver vectors and control block
   int last_iters = 2;
+  int last_broke = 0;            // the last level-1 solve stopped a right-hand side on a breakdown
   CapturedGraph graph;
 };
 

@@ -837,6 +837,7 @@ int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, dou
   const unsigned gt = (unsigned)((nc + 255) / 256);
   DevMem tmp;
   int it;
+  if (A.l2) A.l2->last_broke = 0;
   if (A.vec_prec() == HDCG_F32) {
     tmp.ensure(2 * nc * sizeof(float2));
     float2* bi = tmp.as<float2>();
@@ -844,6 +845,8 @@ int coarse_solve_canon(Ctx& c, Coarse& A, int R, const void* b64, void* x64, dou
     k_canon_to_multi<float2><<<gt, 256, 0, c.stream>>>((const double2*)b64, bi, ne, R);
     it = coarse_cg_multi(c, A, R, bi, xi, tol, maxiter);
     k_multi_to_canon<float2><<<gt, 256, 0, c.stream>>>(xi, (double2*)x64, ne, R);
+    HDCG_REQUIRE(!(A.l2 && A.l2->last_broke), HDCG_ERR_BREAKDOWN,
+                 "level-1 solve: (p, A p) <= 0 or a non-finite residual before the tolerance");
   } else {
     tmp.ensure(2 * nc * sizeof(double2));
     double2* bi = tmp.as<double2>();

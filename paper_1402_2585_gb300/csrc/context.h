@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -38,6 +39,15 @@ inline size_t bytes_per_real(int prec) {
 inline int link_slot(int prec) { return prec == HDCG_BF16T ? HDCG_BF16 : prec == HDCG_DF64 ? 4 : prec; }
 constexpr int NPREC = 6;   // precision codes 0..5 (HDCG_F64 .. HDCG_DF64)
 
+// Process-wide count of device allocations and frees.  A captured CUDA graph
+// holds raw pointers; it is replayed only while this count is unchanged since
+// its capture, so no buffer it may reference can have been freed or moved.
+inline std::atomic<unsigned long long>& alloc_epoch_counter() {
+  static std::atomic<unsigned long long> n{0};
+  return n;
+}
+inline unsigned long long alloc_epoch() { return alloc_epoch_counter().load(); }
+
 // device memory owned by the handle ----------------------------------------------
 struct DevMem {
   void* p = nullptr;
@@ -47,7 +57,10 @@ struct DevMem {
   DevMem& operator=(const DevMem&) = delete;
   ~DevMem() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      ++alloc_epoch_counter();
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -61,6 +74,7 @@ struct DevMem {
       (void)cudaGetLastError();
       throw Error{HDCG_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
     }
+    ++alloc_epoch_counter();
     bytes = n;
   }
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
@@ -220,14 +234,18 @@ struct CapturedGraph {
   }
 };
 
+// key: the pointers and sizes the body uses; the allocation count is added,
+// so any free or reallocation anywhere forces a fresh capture
 template <typename F>
-void run_captured(Ctx& c, CapturedGraph& g, const std::vector<uintptr_t>& key, F&& body) {
+void run_captured(Ctx& c, CapturedGraph& g, const std::vector<uintptr_t>& key_in, F&& body) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (c.stream == nullptr || cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess ||
       cs != cudaStreamCaptureStatusNone) {
     body();
     return;
   }
+  std::vector<uintptr_t> key = key_in;
+  key.push_back((uintptr_t)alloc_epoch());
   if (!g.exec || g.key != key) {
     g.reset();
     const long long l0 = c.launches;

@@ -597,6 +597,7 @@ struct CtlL2 {
   unsigned xm[3][RMAX];     // max |Re|, |Im| of p (0), r (1) and M r (2): tensor-core operand scales
   int iter;
   int all_done;
+  int broke;                // a right-hand side stopped on (p, A p) <= 0 or a NaN above its tolerance
 };
 
 // |b|^2 per right-hand side; x = 0 elsewhere is set by the prolongation of Q2 b
@@ -741,8 +742,10 @@ __global__ void k_l1_update(float2* x, float2* r, const float2* __restrict__ p, 
     for (int q = 0; q < RMAX; ++q) {
       if (q < R) {
         const double rn = ctl->rr[q];
-        if (!ctl->done[q] && (rn <= ctl->stop[q] || it >= maxiter || !(rn == rn) || !(ctl->pAp[q] > 0.0)))
+        if (!ctl->done[q] && (rn <= ctl->stop[q] || it >= maxiter || !(rn == rn) || !(ctl->pAp[q] > 0.0))) {
           ctl->done[q] = 1;
+          if (!(rn <= ctl->stop[q]) && it < maxiter) ctl->broke = 1;
+        }
       }
       all &= ctl->done[q];
     }
@@ -1182,6 +1185,7 @@ int level1_solve(Ctx& c, Coarse& A, int R, const void* rhs, void* sol, double to
     batch = 2;
   }
   L.last_iters = std::max(2, h.iter);
+  L.last_broke = h.broke;
   return h.iter;
 }
 

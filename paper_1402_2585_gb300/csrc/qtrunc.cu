@@ -28,44 +28,57 @@ namespace {
 
 unsigned nblk(size_t n) { return (unsigned)((n + 255) / 256); }
 
-// y[a][j][r] = sum_q sum_k A9[a][q][k][j] x[nb9[a][q]][k][r] + shift x[a][j][r];
-// one CTA per coarse site, up to 4 outputs (j, r) per thread
-__global__ void __launch_bounds__(256) k_qtrunc_apply(const float2* __restrict__ A9, const int* __restrict__ nb9,
-                                                      int nq, int n, const float2* __restrict__ x, int R,
-                                                      float shift, float2* y, const int* skip) {
+// y[a][j][r] = sum_q sum_k A9[a][q][k][j] x[nb9[a][q]][k][r] + shift x[a][j][r],
+// one warp per coarse site: lane l owns the outputs
+// o = o0 + l + 32 u (u < U) of the current chunk, j = o / R, r = o % R.  Each
+// row of a kept block (fixed q and k) is read coalesced across j, x[nb][k][r]
+// is a broadcast within the warp, and no shared memory or barrier is needed.
+template <int U>
+__global__ void __launch_bounds__(256) k_qtrunc_apply_w(const float2* __restrict__ A9, const int* __restrict__ nb9,
+                                                        int nq, int n, const float2* __restrict__ x, int R,
+                                                        float shift, float2* y, const int* skip, size_t Vc) {
   if (skip && *skip) return;
-  extern __shared__ float2 qsm[];
-  float2* As = qsm;            // [k][j] one block
-  float2* xs = qsm + n * n;    // [k][r] neighbour vector
-  const size_t a = blockIdx.x;
+  const size_t a = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (a >= Vc) return;
+  const int lane = threadIdx.x & 31;
   const int nout = n * R;
-  float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int q = 0; q < nq; ++q) {
-    const size_t b = (size_t)nb9[a * 9 + q];
-    __syncthreads();
-    const float2* blk = A9 + (a * 9 + q) * (size_t)n * n;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) As[t] = blk[t];
-    for (int t = threadIdx.x; t < n * R; t += blockDim.x) xs[t] = x[b * n * R + t];
-    __syncthreads();
+  for (int o0 = 0; o0 < nout; o0 += 32 * U) {
+    float ar[U], ai[U];
+    int jo[U], ro[U];
+    bool live[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int o = threadIdx.x + u * blockDim.x;
-      if (o < nout) {
-        const int j = o / R, r = o % R;
-        for (int k = 0; k < n; ++k) {
-          const float2 m = As[k * n + j], v = xs[k * R + r];
-          ar[u] += m.x * v.x - m.y * v.y;
-          ai[u] += m.x * v.y + m.y * v.x;
+    for (int u = 0; u < U; ++u) {
+      const int o = o0 + lane + 32 * u;
+      live[u] = o < nout;
+      jo[u] = live[u] ? o / R : 0;
+      ro[u] = live[u] ? o % R : 0;
+      ar[u] = 0.f;
+      ai[u] = 0.f;
+    }
+    for (int q = 0; q < nq; ++q) {
+      const size_t b = (size_t)__ldg(nb9 + a * 9 + q);
+      const float2* blk = A9 + (a * 9 + q) * (size_t)n * n;
+      const float2* xb = x + b * (size_t)nout;
+#pragma unroll 4
+      for (int k = 0; k < n; ++k) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (live[u]) {
+            const float2 m = __ldg(blk + k * n + jo[u]);
+            const float2 v = __ldg(xb + k * R + ro[u]);
+            ar[u] += m.x * v.x - m.y * v.y;
+            ai[u] += m.x * v.y + m.y * v.x;
+          }
         }
       }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int o = threadIdx.x + u * blockDim.x;
-    if (o < nout) {
-      const float2 v = x[a * nout + o];
-      y[a * nout + o] = make_float2(ar[u] + shift * v.x, ai[u] + shift * v.y);
+    for (int u = 0; u < U; ++u) {
+      if (live[u]) {
+        const size_t o = a * (size_t)nout + o0 + lane + 32 * u;
+        const float2 v = x[o];
+        y[o] = make_float2(ar[u] + shift * v.x, ai[u] + shift * v.y);
+      }
     }
   }
 }
@@ -186,9 +199,18 @@ __global__ void k_pow_norm(const float2* __restrict__ w, float2* v, size_t n, co
 
 void qtrunc_apply(Ctx& c, const Coarse& A, int R, const float2* x, float2* y, double shift, const int* skip) {
   const QTrunc& Q = A.qt;
-  const size_t sm = (size_t)(A.nvec * A.nvec + A.nvec * R) * sizeof(float2);
-  k_qtrunc_apply<<<(unsigned)A.Vc, 256, sm, c.stream>>>(Q.A9.as<float2>(), Q.nb9.as<int>(), Q.nq, A.nvec, x, R,
-                                                         (float)shift, y, skip);
+  const int nout = A.nvec * R;
+  const unsigned grid = (unsigned)((A.Vc + 7) / 8);
+  if (nout <= 32)
+    k_qtrunc_apply_w<1><<<grid, 256, 0, c.stream>>>(Q.A9.as<float2>(), Q.nb9.as<int>(), Q.nq, A.nvec, x, R,
+                                                   (float)shift, y, skip, A.Vc);
+  else if (nout <= 64)
+    k_qtrunc_apply_w<2><<<grid, 256, 0, c.stream>>>(Q.A9.as<float2>(), Q.nb9.as<int>(), Q.nq, A.nvec, x, R,
+                                                   (float)shift, y, skip, A.Vc);
+  else
+    k_qtrunc_apply_w<4><<<grid, 256, 0, c.stream>>>(Q.A9.as<float2>(), Q.nb9.as<int>(), Q.nq, A.nvec, x, R,
+                                                   (float)shift, y, skip, A.Vc);
+  HDCG_CUDA(cudaGetLastError());
   ++c.launches;
 }
 
