@@ -20,10 +20,11 @@
 // operator is split into FP16 hi + lo parts (about 22 significant bits) that
 // enter as two MMAs against the same B tile; an FP16 operator is one part.
 //
-// With Nvec = 32 a block has 64 rows, so two coarse sites share one M = 128
-// MMA (rows 0..63 site a0, 64..127 site a1) against B = [B_{a0+l} | B_{a1+l}];
-// the two off-diagonal quadrants of D are discarded.  Otherwise one site per
-// MMA: its 2 Nvec rows are stored and the MMA's remaining rows are discarded.
+// With Nvec <= 32 a block has at most 64 rows, so two coarse sites share one
+// M = 128 MMA (rows 0..63 site a0, 64..127 site a1) against B = [B_{a0+l} |
+// B_{a1+l}]; the two off-diagonal quadrants of D are discarded.  Above 32 one
+// site per MMA: its 2 Nvec rows are stored and the MMA's remaining rows are
+// discarded.
 // K = Nvec padded to a multiple of 16.  Both operands are pre-tiled in global
 // memory in the no-swizzle K-major core-matrix layout, so every stage of the
 // pipeline is filled by plain bulk copies: the A blocks of the sites (the HBM
@@ -78,10 +79,10 @@ TcGeom tc_geom(int nvec, int R, int parts, uint32_t ring_bytes) {
   HDCG_REQUIRE(nvec >= 1 && nvec <= 64, HDCG_ERR_ARG, "tensor-core coarse operator needs Nvec <= 64");
   HDCG_REQUIRE(R >= 1 && R <= TC_RPMAX, HDCG_ERR_ARG, "1..16 right-hand sides");
   TcGeom g;
-  // two sites share an MMA only when they fill its 128 rows exactly (Nvec 32);
-  // otherwise one site per MMA with the compact layout below, which copies
+  // two sites share an MMA for Nvec <= 32 (exactly its 128 rows at Nvec 32);
+  // one site per MMA above that, with the compact layout below, which copies
   // only the operator's bytes
-  g.sites = nvec == 32 ? 2 : 1;
+  g.sites = nvec <= 32 ? 2 : 1;
   g.MS = 128 / g.sites;
   g.Kp = (nvec + 15) / 16 * 16;
   const int q = g.sites == 2 ? 2 : 4;   // keeps N = sites * 4 Rp a multiple of 16

@@ -80,7 +80,7 @@ def _multi(torch, h, X):
 @pytest.mark.parametrize("nvec", [32, 40, 6])
 @pytest.mark.parametrize("R", [1, 3, 12, 16])
 def test_tensor_core_multi_apply(geom, nvec, R):
-    """Two coarse sites per M = 128 MMA (Nvec 32) and one site (Nvec 6, 40);
+    """Two coarse sites per M = 128 MMA (Nvec 32, 6) and one site (Nvec 40);
     padded K (Nvec 6, 40); ragged site pair (Vc odd); N = 8 Rp from 16 to 128."""
     torch, bl, h, A = _handle(geom, nvec, F16)
     X = sy.complex_normal(920 + R, (R, bl.Vc, nvec))
