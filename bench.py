@@ -53,7 +53,7 @@ PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 # property of the algorithm on that input).  The reference arm, which runs no
 # GPU code, scales the oracle's per-apply time by it; the GPU arm reports its
 # measured count beside this figure (``h_applies_per_rhs``).
-H_APPLIES_PER_RHS = {DEFAULT_WORKLOAD: 1211, "cfg2_16x16x16x16_ls16_shamir": 140}
+H_APPLIES_PER_RHS = {DEFAULT_WORKLOAD: 824, "cfg2_16x16x16x16_ls16_shamir": 140}
 
 # DRAM bytes (read + write) per hop_kernel launch of the outer precision from
 # one ncu capture of the current kernel, per workload; None once the kernel
