@@ -190,8 +190,8 @@ typedef struct {
  * truncated to surface_depth and block-orthonormalised.  Method
  * HDCG_SUBSPACE_CONTINUE applies inv_steps inverse-iteration steps of shift
  * inv_shift to the current subspace (e.g. one promoted by
- * hdcg_promote_subspace), then the truncation and block Gram-Schmidt.  Level 2 (three-level HDCG): the
- * same construction on the coarse lattice, Sec. 2 applied to the little Dirac
+ * hdcg_promote_subspace), then the truncation and block Gram-Schmidt.
+ * Level 2 (three-level HDCG): the same construction on the coarse lattice, Sec. 2 applied to the little Dirac
  * operator; each step solves (A + inv_shift) for up to 16 vectors at once
  * (coarse CG), and the start vectors are the splitmix64 stream seed in
  * canonical order [k][Vc][Nvec].  Level 2 needs the level-1 operator (FP32 or
@@ -231,7 +231,9 @@ int hdcg_get_subspace(hdcg_t h, int level, void* phi_host);
  * stored in prec (HDCG_F32 or HDCG_F64; Vc2 * Nvec2 <= 65536).  From then on
  * every coarse solve (the inversion of A inside Q, and hdcg_coarse_solve) is
  * A-DEF2 on A with Q2 = P2 A2^-1 R2 and M = 1 (Fig. pcg_general, Table algos):
- * x0 = Q2 b, y = r + Q2 (r - A r), flexible beta.  HDCG_ERR_BREAKDOWN if A2 has
+ * x0 = Q2 b, y = r + Q2 (r - A r), flexible beta; or with M the Chebyshev
+ * polynomial of Q_trunc (hdcg_set_coarse_preconditioner): y = z + Q2 (r - A z),
+ * z = M r.  HDCG_ERR_BREAKDOWN if A2 has
  * a non-positive diagonal or a zero pivot.  Synchronous. */
 int hdcg_build_coarse(hdcg_t h, int level, int prec);
 
