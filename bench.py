@@ -543,6 +543,7 @@ def run_ours(args, w):
         "reliable_delta": args.reliable_delta,
     }
     line["roofline"] = roofline(w, hop_all, sloppy, peak, peak_kind, nrhs)
+    line["hop_flops"] = hop_flop_rate(w, hop_all, sloppy)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -572,6 +573,18 @@ def coarse_roofline(h, w, args):
                           "GBps": bytes_ / t / 1e9, "frac": bytes_ / t / 1e9 / peak,
                           "tflops": 8.0 * vc * 81 * w.nvec ** 2 * R / t / 1e12}
     return out
+
+
+def hop_flop_rate(w, hop_all, pname):
+    """Flop rate of the roofline kernel's launches: every four launches are one
+    H over the lattice's odd 5D sites (the bench's solves have one right-hand
+    side), at hop_flops_per_site flops per site."""
+    hp = hop_all.get(pname)
+    if not hp or hp["ms"] <= 0:
+        return None
+    flops = hp["launches"] / 4.0 * n5_of(w) * hop_flops_per_site(w)
+    return {"flop_per_site_per_H": hop_flops_per_site(w), "achieved": flops / (hp["ms"] / 1e3) / 1e12,
+            "unit": "TFLOP/s", "kernel": f"hop_kernel ({pname} storage), the roofline kernel's launches"}
 
 
 def roofline(w, hop_all, pname, peak, peak_kind, nrhs):
